@@ -1,0 +1,203 @@
+/*
+ * pint.h -- C ABI of the GB300 parallel-in-time KKT solver for unsteady
+ * Stokes / Oseen distributed optimal control (Heinzelreiter & Pearson,
+ * "Diagonalization-Based Parallel-in-Time Preconditioners for Instationary
+ * Fluid Flow Control Problems").
+ *
+ * The library solves the all-at-once optimality system of Sec. 2 (Eq. FinalA)
+ * with flexible GMRES (Sec. 3.4), preconditioned by the block-circulant
+ * approximation P_C of Sec. 3.1 whose frequency blocks (Eq. SubBlockG) are
+ * handled by the Stokes transform and commutator preconditioner (Sec. 3.2,
+ * Algorithms 1-2) or the Uzawa-based preconditioner of Sec. 4 (Algorithm 3).
+ *
+ * Conventions (all entry points)
+ *  - Every call returns a pint_status; PINT_OK = 0.  No exception or C++
+ *    object crosses the ABI.  On failure pint_last_error(h) (or
+ *    pint_last_error(NULL) when no handle exists yet) returns a message that
+ *    stays valid until the next call on the same thread.
+ *  - Device pointers ("_dev") are CUDA global-memory addresses on the device
+ *    that was current at pint_create; host pointers ("_host") are ordinary
+ *    host memory.  The caller owns every buffer it passes; the library owns
+ *    (allocates at create, frees at destroy) all of its internal workspace.
+ *  - All device work is enqueued on the stream given to pint_create.  Entry
+ *    points that return numbers to the host (solve, the GMRES loops inside
+ *    apply_preconditioner) synchronise that stream.  A handle is not
+ *    thread-safe; distinct handles may be used from distinct threads.
+ *  - Time-domain all-at-once vectors ("KKT vectors") are real FP64 arrays
+ *    [n_t][n_blk], one block per time level t_k = k tau (k = 1..n_t), each
+ *    block holding six fields back to back:
+ *        v_x, v_y (Q2, n_s = (2N+1)^2 nodes each), p (Q1, n_q = (N+1)^2),
+ *        lambda_x, lambda_y (Q2), mu (Q1);
+ *    node index = iy * (nodes per side) + ix on the uniform grid over
+ *    [x0, x1]^2.  Residual vectors use the same slots: the adjoint-equation
+ *    rows (first block row of Eq. FinalA) in the (v, p) slots, the
+ *    state-equation rows in the (lambda, mu) slots.  Dirichlet velocity
+ *    nodes (the boundary) and the pinned pressure node (the Q1 node at
+ *    (x0, x0), index 0) are not unknowns: their input entries are ignored
+ *    and their output entries are written as 0.
+ *  - Frequency-domain vectors are complex FP64 (interleaved re, im) arrays
+ *    [J][n_blk][2] with J = floor(n_t/2) + 1 (the Hermitian half of the
+ *    spectrum; frequency n_t - j is the conjugate of j), same slots.
+ */
+#ifndef PINT_H
+#define PINT_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pint_ctx* pint_handle;
+
+typedef enum {
+  PINT_OK = 0,
+  PINT_ERR_ARG = 1,            /* invalid argument or parameter            */
+  PINT_ERR_OOM = 2,            /* device or host allocation failed         */
+  PINT_ERR_CUDA = 3,           /* a CUDA call failed (message has details) */
+  PINT_ERR_NOT_CONVERGED = 4,  /* outer solve hit outer_maxit             */
+  PINT_ERR_NONFINITE = 5,      /* NaN/Inf in host input data              */
+  PINT_ERR_TIMEOUT = 6,        /* a bounded device wait gave up            */
+  PINT_ERR_STATE = 7           /* call out of order (e.g. solve before set_data) */
+} pint_status;
+
+typedef enum { PINT_STOKES = 0, PINT_OSEEN = 1 } pint_kind;
+
+/* Wind of the Oseen operator (Sec. 2).  RECIRC is w = (2y(1-x^2), -2x(1-y^2)),
+ * divergence free and tangential on the boundary of [-1,1]^2; it requires
+ * x0 = -1, x1 = 1. */
+typedef enum { PINT_WIND_NONE = 0, PINT_WIND_RECIRC = 1 } pint_wind;
+
+/* Arithmetic of the preconditioner.  The outer FGMRES (Arnoldi,
+ * least-squares update, true residual) and the multigrid coarse solve are
+ * FP64 in both modes. */
+typedef enum { PINT_PREC_FP64 = 0, PINT_PREC_FP32 = 1 } pint_prec;
+
+typedef struct {
+  int kind;            /* pint_kind                                          */
+  int level;           /* N = 2^level elements per side, 1 <= level <= 10    */
+  double x0, x1;       /* square domain [x0, x1]^2                           */
+  int n_t;             /* number of time blocks K (size of I_t, E, C; Sec. 2.2) */
+  double tau;          /* time step                                          */
+  double beta;         /* control regularisation (Eq. OseenOptimization)     */
+  double nu;           /* viscosity; L = nu K + N(w)                         */
+  int wind;            /* pint_wind                                          */
+  int prec;            /* pint_prec                                          */
+  int outer_restart;   /* FGMRES restart length m (Sec. 3.4)                 */
+  int outer_maxit;     /* total outer iterations allowed                     */
+  double outer_tol;    /* stop when ||b - A x||_2 / ||b||_2 <= outer_tol     */
+  double inner_tol;    /* inner GMRES tolerance epsilon (Sec. 3.4, 5.1.2)    */
+  int inner_maxit;     /* inner GMRES iteration cap (no restart)             */
+  int mg_cycles;       /* V-cycles per multigrid application (Sec. 5.1.1: 4) */
+  int mg_pre, mg_post; /* multicolour SOR sweeps before / after correction   */
+  int cheb_steps;      /* Chebyshev semi-iteration steps (Sec. 5.1.1: 10)    */
+  int uzawa_steps;     /* Uzawa steps in Algorithm 3 (Sec. 5.2.1: 6)         */
+  double uzawa_mu;     /* Uzawa parameter mu (Sec. 4: 3/4)                   */
+  double sor_omega;    /* SOR relaxation (1 = Gauss-Seidel)                  */
+  int fixed_inner_its; /* > 0: run exactly this many inner GMRES iterations  */
+  int linear;          /* 1: Algorithm 1 (no inner GMRES), 0: Algorithm 2/3  */
+} pint_params;
+
+typedef struct {
+  int outer_iterations;   /* FGMRES iterations taken                         */
+  int restarts;
+  double relres;          /* true ||b - A x|| / ||b|| at return (FP64)       */
+  double relres_history[256]; /* Arnoldi estimates, first 256 iterations     */
+  int inner_iterations_total; /* sum over applications and frequencies      */
+  int inner_iterations_max;   /* largest per-frequency count in one apply   */
+  int precond_applies;
+  double ms_precond, ms_matvec, ms_orth, ms_total; /* host wall-clock split */
+} pint_solve_info;
+
+typedef struct {
+  int N, n_t, J;
+  size_t n_s, n_q, n_blk;     /* per-field / per-block sizes (see header)   */
+  size_t kkt_len;             /* n_t * n_blk doubles                         */
+  size_t freq_len;            /* J * n_blk complex values                    */
+  size_t device_bytes;        /* workspace owned by the handle              */
+} pint_sizes;
+
+/* Defaults from Sec. 5: FGMRES(30), inner tolerance 1e-2, 4 V-cycles with
+ * 2+2 SOR sweeps (omega = 1), 10 Chebyshev steps, 6 Uzawa steps, mu = 3/4,
+ * inner cap 100, outer tolerance 1e-8.  Problem fields are set to a Stokes
+ * problem on [0,1]^2 with N = 8, n_t = 8, tau = 1/9, beta = 1e-2, nu = 1e-2. */
+void pint_default_params(pint_params* p);
+
+/* Create a problem (Sec. 2.2 discretisation, Sec. 3 preconditioner setup).
+ * stream: a cudaStream_t (NULL = legacy default stream).  Allocates all
+ * device workspace; returns PINT_ERR_ARG for invalid parameters,
+ * PINT_ERR_OOM if the workspace does not fit. */
+pint_status pint_create(const pint_params* p, void* stream, pint_handle* out);
+
+/* Frees everything the handle owns.  Accepts NULL. */
+pint_status pint_destroy(pint_handle h);
+
+pint_status pint_get_sizes(pint_handle h, pint_sizes* s);
+
+/* Problem data (Sec. 2.2 backward-Euler equations): builds the right-hand
+ * side b on the device.  vd_host: desired velocity [n_t][2][n_s] at
+ * t_k = k tau; f_host: forcing [n_t][2][n_s] or NULL; v0_host: initial
+ * velocity [2][n_s] or NULL.  Adjoint rows get tau M v_d(t_k), state rows
+ * tau M f(t_k), the first state row also M v_0.  PINT_ERR_NONFINITE on
+ * NaN/Inf input. */
+pint_status pint_set_data(pint_handle h, const double* vd_host, const double* f_host,
+                          const double* v0_host);
+
+/* Copy the assembled right-hand side b (KKT vector) to b_dev. */
+pint_status pint_get_rhs(pint_handle h, double* b_dev);
+
+/* y = A x with A of Eq. FinalA, FP64, matrix-free.  x_dev, y_dev: KKT
+ * vectors (must not overlap). */
+pint_status pint_kkt_matvec(pint_handle h, const double* x_dev, double* y_dev);
+
+/* z = P^{-1} r: the parallel-in-time preconditioner (Algorithm 1 if
+ * params.linear, else Algorithm 2 (Stokes) / the Uzawa variant (Oseen)),
+ * in the handle's precision.  r_dev, z_dev: KKT vectors. */
+pint_status pint_apply_preconditioner(pint_handle h, const double* r_dev, double* z_dev);
+
+/* Solve A x = b by FP64 FGMRES(m) with the preconditioner.  x_dev: in =
+ * initial guess, out = solution (KKT vector).  info may be NULL.  Returns
+ * PINT_ERR_NOT_CONVERGED (with x the last iterate) if outer_maxit is hit. */
+pint_status pint_solve(pint_handle h, double* x_dev, pint_solve_info* info);
+
+/* Same as pint_solve with host buffers: copies the initial guess host to
+ * device, solves, copies the solution back (synchronous). */
+pint_status pint_solve_host(pint_handle h, double* x_host, pint_solve_info* info);
+
+/* ---- component entry points (diagnostics and parity testing) ------------ */
+
+/* xhat = F x along time (Sec. 3.1, F_jk = exp(-2 pi i j k / n_t)) for the
+ * Hermitian half j = 0..J-1; x_dev: KKT vector; xhat_dev: frequency vector. */
+pint_status pint_dft_forward(pint_handle h, const double* x_dev, double* xhat_dev);
+
+/* x = Re F^{-1} xhat, using the conjugate symmetry of the full spectrum. */
+pint_status pint_dft_inverse(pint_handle h, const double* xhat_dev, double* x_dev);
+
+/* y_j = G_j x_j (Eq. SubBlockG) for every frequency of the half spectrum;
+ * frequency vectors in the library slot order (rows in the slot order of
+ * the residual convention above). */
+pint_status pint_freq_block_matvec(pint_handle h, const double* xhat_dev, double* yhat_dev);
+
+/* The frequency part of the preconditioner: for every j, y_j = the block
+ * solve of Algorithm 1/2 (Stokes: (T^r)^{-1} Zbar_j^{-1} (T^l)^{-1}) or of
+ * Algorithm 3 inside inner GMRES (Oseen), on frequency vectors.
+ * inner_its_host: NULL or int[J] receiving the inner GMRES counts. */
+pint_status pint_freq_block_solve(pint_handle h, const double* rhat_dev, double* yhat_dev,
+                                  int* inner_its_host);
+
+/* Component operators on one frequency's fields (complex FP64 in/out, full
+ * grid, interleaved): which =
+ *   0  multigrid on W_j  (Q2 field, Sec. 3.2)      1  multigrid on Q_j (Sec. 4)
+ *   2  multigrid on Q_j^H                          3  multigrid on K_p (Q1 field)
+ *   4  Chebyshev on M (Q2 field)                   5  Chebyshev on M_p (Q1 field)
+ *   6  block preconditioner P~_j (Stokes) / P~_j^(UZ) (Oseen), frequency block
+ * j selects the frequency (0 <= j < J).  Runs in the handle's precision. */
+pint_status pint_component_apply(pint_handle h, int which, int j, const double* in_dev,
+                                 double* out_dev);
+
+const char* pint_last_error(pint_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PINT_H */

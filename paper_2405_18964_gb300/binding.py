@@ -1,0 +1,231 @@
+"""ctypes binding of the C ABI in include/pint.h (argument marshalling only).
+
+Every computation runs in libpint.so's CUDA kernels; this module only turns
+Python arguments into the C structs and pointers the ABI takes.  Device
+buffers are torch CUDA tensors (float64, or complex128 for frequency
+vectors), passed by their data pointers; host buffers are numpy arrays.
+Importing this module does not load the library; the first call does, and it
+raises if libpint.so has not been built.
+"""
+import ctypes
+import os
+import re
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libpint.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "pint.h")
+
+PINT_STOKES, PINT_OSEEN = 0, 1
+PINT_WIND_NONE, PINT_WIND_RECIRC = 0, 1
+PINT_PREC_FP64, PINT_PREC_FP32 = 0, 1
+STATUS = {0: "PINT_OK", 1: "PINT_ERR_ARG", 2: "PINT_ERR_OOM", 3: "PINT_ERR_CUDA", 4: "PINT_ERR_NOT_CONVERGED",
+          5: "PINT_ERR_NONFINITE", 6: "PINT_ERR_TIMEOUT", 7: "PINT_ERR_STATE"}
+COMPONENT = {"mg_W": 0, "mg_Q": 1, "mg_QH": 2, "mg_Kp": 3, "cheb_M": 4, "cheb_Mp": 5, "block_prec": 6}
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("level", ctypes.c_int), ("x0", ctypes.c_double), ("x1", ctypes.c_double),
+                ("n_t", ctypes.c_int), ("tau", ctypes.c_double), ("beta", ctypes.c_double), ("nu", ctypes.c_double),
+                ("wind", ctypes.c_int), ("prec", ctypes.c_int), ("outer_restart", ctypes.c_int),
+                ("outer_maxit", ctypes.c_int), ("outer_tol", ctypes.c_double), ("inner_tol", ctypes.c_double),
+                ("inner_maxit", ctypes.c_int), ("mg_cycles", ctypes.c_int), ("mg_pre", ctypes.c_int),
+                ("mg_post", ctypes.c_int), ("cheb_steps", ctypes.c_int), ("uzawa_steps", ctypes.c_int),
+                ("uzawa_mu", ctypes.c_double), ("sor_omega", ctypes.c_double), ("fixed_inner_its", ctypes.c_int),
+                ("linear", ctypes.c_int)]
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("outer_iterations", ctypes.c_int), ("restarts", ctypes.c_int), ("relres", ctypes.c_double),
+                ("relres_history", ctypes.c_double * 256), ("inner_iterations_total", ctypes.c_int),
+                ("inner_iterations_max", ctypes.c_int), ("precond_applies", ctypes.c_int),
+                ("ms_precond", ctypes.c_double), ("ms_matvec", ctypes.c_double), ("ms_orth", ctypes.c_double),
+                ("ms_total", ctypes.c_double)]
+
+
+class Sizes(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int), ("n_t", ctypes.c_int), ("J", ctypes.c_int), ("n_s", ctypes.c_size_t),
+                ("n_q", ctypes.c_size_t), ("n_blk", ctypes.c_size_t), ("kkt_len", ctypes.c_size_t),
+                ("freq_len", ctypes.c_size_t), ("device_bytes", ctypes.c_size_t)]
+
+
+_lib = None
+_P = ctypes.c_void_p
+_SIGS = {
+    "pint_default_params": (None, [ctypes.POINTER(Params)]),
+    "pint_create": (ctypes.c_int, [ctypes.POINTER(Params), _P, ctypes.POINTER(_P)]),
+    "pint_destroy": (ctypes.c_int, [_P]),
+    "pint_get_sizes": (ctypes.c_int, [_P, ctypes.POINTER(Sizes)]),
+    "pint_set_data": (ctypes.c_int, [_P, _P, _P, _P]),
+    "pint_get_rhs": (ctypes.c_int, [_P, _P]),
+    "pint_kkt_matvec": (ctypes.c_int, [_P, _P, _P]),
+    "pint_apply_preconditioner": (ctypes.c_int, [_P, _P, _P]),
+    "pint_solve": (ctypes.c_int, [_P, _P, ctypes.POINTER(SolveInfo)]),
+    "pint_solve_host": (ctypes.c_int, [_P, _P, ctypes.POINTER(SolveInfo)]),
+    "pint_dft_forward": (ctypes.c_int, [_P, _P, _P]),
+    "pint_dft_inverse": (ctypes.c_int, [_P, _P, _P]),
+    "pint_freq_block_matvec": (ctypes.c_int, [_P, _P, _P]),
+    "pint_freq_block_solve": (ctypes.c_int, [_P, _P, _P, _P]),
+    "pint_component_apply": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P, _P]),
+    "pint_last_error": (ctypes.c_char_p, [_P]),
+}
+
+
+def header_functions():
+    """Names of the functions include/pint.h declares."""
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(pint_[a-z0-9_]+)\s*\(", txt)))
+
+
+def lib():
+    """Load libpint.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libpint.so not found: build it with __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+class PintError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+def _check(code, handle=None):
+    if code != 0:
+        msg = lib().pint_last_error(handle)
+        raise PintError(code, msg.decode() if msg else "")
+    return code
+
+
+def _dptr(t, dtype_name, numel=None):
+    """Device pointer of a contiguous CUDA tensor of the given dtype."""
+    if not hasattr(t, "data_ptr") or not t.is_cuda:
+        raise TypeError("expected a CUDA tensor")
+    if str(t.dtype) != "torch." + dtype_name:
+        raise TypeError(f"expected torch.{dtype_name}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise TypeError("expected a contiguous tensor")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"expected {numel} elements, got {t.numel()}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _hptr(a, numel=None):
+    if a is None:
+        return None
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if numel is not None and a.size != numel:
+        raise ValueError(f"expected {numel} values, got {a.size}")
+    return a
+
+
+def default_params(**kw):
+    p = Params()
+    lib().pint_default_params(ctypes.byref(p))
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise AttributeError(f"unknown parameter {k}")
+        setattr(p, k, v)
+    return p
+
+
+class Problem:
+    """One discrete control problem on the GPU (handle of the C ABI)."""
+
+    def __init__(self, params, stream=None):
+        self.params = params
+        h = ctypes.c_void_p()
+        st = ctypes.c_void_p(stream) if stream else None
+        _check(lib().pint_create(ctypes.byref(params), st, ctypes.byref(h)))
+        self.h = h
+        s = Sizes()
+        _check(lib().pint_get_sizes(self.h, ctypes.byref(s)), self.h)
+        self.sizes = s
+
+    def close(self):
+        if self.h:
+            lib().pint_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # shapes
+    @property
+    def kkt_len(self):
+        return self.sizes.kkt_len
+
+    @property
+    def freq_len(self):
+        return self.sizes.freq_len
+
+    def set_data(self, vd, f=None, v0=None):
+        K, ns = self.sizes.n_t, self.sizes.n_s
+        vd = _hptr(vd, K * 2 * ns)
+        f = _hptr(f, K * 2 * ns)
+        v0 = _hptr(v0, 2 * ns)
+        ptr = lambda a: a.ctypes.data_as(ctypes.c_void_p) if a is not None else None
+        _check(lib().pint_set_data(self.h, ptr(vd), ptr(f), ptr(v0)), self.h)
+
+    def get_rhs(self, b):
+        _check(lib().pint_get_rhs(self.h, _dptr(b, "float64", self.kkt_len)), self.h)
+
+    def kkt_matvec(self, x, y):
+        _check(lib().pint_kkt_matvec(self.h, _dptr(x, "float64", self.kkt_len), _dptr(y, "float64", self.kkt_len)),
+               self.h)
+
+    def apply_preconditioner(self, r, z):
+        _check(lib().pint_apply_preconditioner(self.h, _dptr(r, "float64", self.kkt_len),
+                                               _dptr(z, "float64", self.kkt_len)), self.h)
+
+    def solve(self, x, check=True):
+        info = SolveInfo()
+        code = lib().pint_solve(self.h, _dptr(x, "float64", self.kkt_len), ctypes.byref(info))
+        if check:
+            _check(code, self.h)
+        return info
+
+    def solve_host(self, x, check=True):
+        a = np.ascontiguousarray(x, dtype=np.float64)
+        if a.size != self.kkt_len or a is not x:
+            raise ValueError("x must be a contiguous float64 array of kkt_len values")
+        info = SolveInfo()
+        code = lib().pint_solve_host(self.h, a.ctypes.data_as(ctypes.c_void_p), ctypes.byref(info))
+        if check:
+            _check(code, self.h)
+        return info
+
+    def dft_forward(self, x, xhat):
+        _check(lib().pint_dft_forward(self.h, _dptr(x, "float64", self.kkt_len),
+                                      _dptr(xhat, "complex128", self.freq_len)), self.h)
+
+    def dft_inverse(self, xhat, x):
+        _check(lib().pint_dft_inverse(self.h, _dptr(xhat, "complex128", self.freq_len),
+                                      _dptr(x, "float64", self.kkt_len)), self.h)
+
+    def freq_block_matvec(self, xhat, yhat):
+        _check(lib().pint_freq_block_matvec(self.h, _dptr(xhat, "complex128", self.freq_len),
+                                            _dptr(yhat, "complex128", self.freq_len)), self.h)
+
+    def freq_block_solve(self, rhat, yhat):
+        its = (ctypes.c_int * self.sizes.J)()
+        _check(lib().pint_freq_block_solve(self.h, _dptr(rhat, "complex128", self.freq_len),
+                                           _dptr(yhat, "complex128", self.freq_len), its), self.h)
+        return list(its)
+
+    def component_apply(self, which, j, x, y):
+        w = COMPONENT[which] if isinstance(which, str) else int(which)
+        _check(lib().pint_component_apply(self.h, w, j, _dptr(x, "complex128"), _dptr(y, "complex128")), self.h)

@@ -1,0 +1,1211 @@
+// api.cu -- problem context, solver orchestration and the C ABI (pint.h).
+//
+// Flow of one solve (Sec. 3-4 of the paper):
+//   FP64 FGMRES(m) on the KKT system of Eq. FinalA (matrix-free matvec)
+//     z = P^{-1} v :  r^ = F v (time DFT, Hermitian half)
+//                     Stokes: s^_j = (T_j^l)^{-1} r^_j ; x^_j = GMRES(Z_j, P~_j, s^_j, eps)
+//                             y^_j = (T_j^r)^{-1} x^_j                    (Algorithm 2)
+//                     Oseen:  y^_j = GMRES(G_j, P~_j^(UZ), r^_j, eps)      (Algorithm 3)
+//                     z = Re F^{-1} y^
+// Every frequency is processed in the same launches; converged frequencies
+// drop out through a device-side active mask.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "fields.h"
+#include "kernels.h"
+#include "krylov.h"
+#include "pint.h"
+#include "tables.h"
+
+using namespace pint;
+
+namespace {
+thread_local std::string g_err;
+
+// Wathen's bounds on the spectrum of diag(M)^{-1} M for the bilinear and
+// biquadratic elements (Sec. 3.4 cites them for the Chebyshev iteration).
+constexpr double Q2_LMIN = 0.25, Q2_LMAX = 1.5625;
+constexpr double Q1_LMIN = 0.25, Q1_LMAX = 2.25;
+
+struct Status {
+  pint_status code;
+  std::string msg;
+};
+}  // namespace
+
+struct pint_ctx;
+
+template <class T>
+struct Engine {
+  pint_ctx* c = nullptr;
+  Tabs<T> tabs{};
+  cpx<T>* R = nullptr;  // frequency vectors [J][nblk]
+  cpx<T>* Y = nullptr;
+  cpx<T>* T1 = nullptr;
+  cpx<T>* T2 = nullptr;
+  cpx<T>* T3 = nullptr;
+  cpx<T>* V = nullptr;  // inner GMRES basis [m+1][J][nblk]
+  cpx<T>* Z = nullptr;  // [m][J][nblk]
+  cpx<T>* mgws = nullptr;
+  cpx<T>* chebws = nullptr;
+  T* cosk = nullptr;
+  T* sink = nullptr;
+
+  void mg(int space, bool conv, const FieldJob* jobs, int njobs, cpx<T>* xb, const cpx<T>* bb, const int* active);
+  void cheb(int space, const FieldJob* jobs, int njobs, cpx<T>* xb, const cpx<T>* bb, const int* active);
+  void block_prec(const cpx<T>* U, cpx<T>* Out, const int* active);
+  void block_matvec(const BlkCoef* coef, const cpx<T>* X, cpx<T>* Out, const int* active);
+  void inner_solve(const cpx<T>* S, cpx<T>* X, int* its_host);
+  void freq_solve(cpx<T>* Rin, cpx<T>* Out, int* its_host);
+  void apply(const double* r, double* z, int* its_host);
+};
+
+struct pint_ctx {
+  pint_params p{};
+  cudaStream_t st = nullptr;
+  int N = 0, K = 0, J = 0, nlev = 0, m_in = 0;
+  Slots s{};
+  bool oseen = false, conv = false, fp32 = false;
+  std::vector<void*> allocs;
+  size_t dev_bytes = 0;
+  std::string err;
+
+  Tabs<double> t64{};
+  Tabs<float> t32{};
+  MGLayout lay2{}, lay1{};
+  long long cheb_per_q2 = 0, cheb_per_q1 = 0;
+
+  OpCoef* d_ops = nullptr;
+  int nops = 0;
+  double* d_cinv = nullptr;
+  BlkCoef* d_blkZ = nullptr;  // inner operator (Z_j Stokes / G_j Oseen)
+  BlkCoef* d_blkG = nullptr;  // G_j (Eq. SubBlockG)
+  double* d_tc = nullptr;     // Stokes transform constants [J][3]
+  double* d_sa = nullptr;     // Stokes Schur combination (1 + c1)   [J] complex
+  double* d_sb = nullptr;     // Stokes Schur combination nu c2     [J] complex
+  double* d_one = nullptr;    // [J] complex 1
+  double* d_invtau = nullptr; // [J] complex 1/tau
+  double* d_mtaumu = nullptr; // [J] complex -tau/mu
+  OpCoef *d_cuza = nullptr, *d_cuzd = nullptr, *d_cmass = nullptr, *d_cxp = nullptr;
+  FieldJob *j_W4 = nullptr, *j_Q2 = nullptr, *j_QH2 = nullptr, *j_M2 = nullptr, *j_Kp2 = nullptr,
+           *j_Mp2 = nullptr, *j_Kp2s = nullptr, *j_Mp2s = nullptr, *j_one = nullptr;
+  int* d_active_one = nullptr;
+  GmresState gs{};
+
+  // outer FGMRES (FP64)
+  double *oV = nullptr, *oZ = nullptr, *ob = nullptr, *ox = nullptr, *ot = nullptr, *opart = nullptr,
+         *oh = nullptr;
+  double* ofreq = nullptr;  // FP64 complex [J][nblk] staging for frequency-domain inputs
+  double* h_pinned = nullptr;
+  int* h_count = nullptr;
+  bool have_data = false;
+
+  Engine<double> e64;
+  Engine<float> e32;
+
+  // ----------------------------------------------------------- helpers
+  pint_status fail(pint_status code, const std::string& m) {
+    err = m;
+    g_err = m;
+    return code;
+  }
+  bool cu(cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return true;
+    err = std::string(what) + ": " + cudaGetErrorString(e);
+    g_err = err;
+    return false;
+  }
+  template <class P>
+  bool alloc(P** ptr, size_t bytes) {
+    void* v = nullptr;
+    if (bytes == 0) bytes = 16;
+    if (cudaMalloc(&v, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    allocs.push_back(v);
+    dev_bytes += bytes;
+    *ptr = static_cast<P*>(v);
+    return true;
+  }
+  template <class P>
+  bool upload(P** ptr, const std::vector<P>& host) {
+    if (!alloc(ptr, host.size() * sizeof(P))) return false;
+    return cudaMemcpy(*ptr, host.data(), host.size() * sizeof(P), cudaMemcpyHostToDevice) == cudaSuccess;
+  }
+  bool launched(const char* what) { return cu(cudaGetLastError(), what); }
+};
+
+// ============================================================================
+// Engine<T>
+// ============================================================================
+template <class T>
+static Tabs<T>& tabs_of(pint_ctx* c);
+template <>
+Tabs<double>& tabs_of<double>(pint_ctx* c) {
+  return c->t64;
+}
+template <>
+Tabs<float>& tabs_of<float>(pint_ctx* c) {
+  return c->t32;
+}
+
+template <class T>
+void Engine<T>::mg(int space, bool conv, const FieldJob* jobs, int njobs, cpx<T>* xb, const cpx<T>* bb,
+                   const int* active) {
+  MGLaunch<T> L{};
+  L.tabs = tabs;
+  L.lay = space == 2 ? c->lay2 : c->lay1;
+  L.ops = c->d_ops;
+  L.coarse_inv = c->d_cinv;
+  L.jobs = jobs;
+  L.njobs = njobs;
+  L.xbase = xb;
+  L.bbase = bb;
+  L.ws = mgws;
+  L.active = active;
+  L.cycles = c->p.mg_cycles;
+  L.pre = c->p.mg_pre;
+  L.post = c->p.mg_post;
+  L.omega = c->p.sor_omega;
+  L.space = space;
+  L.conv = conv;
+  launch_mg<T>(L, c->st);
+}
+
+template <class T>
+void Engine<T>::cheb(int space, const FieldJob* jobs, int njobs, cpx<T>* xb, const cpx<T>* bb, const int* active) {
+  ChebLaunch<T> L{};
+  L.tabs = tabs;
+  L.jobs = jobs;
+  L.njobs = njobs;
+  L.xbase = xb;
+  L.bbase = bb;
+  L.ws = chebws;
+  L.per_job = space == 2 ? c->cheb_per_q2 : c->cheb_per_q1;
+  L.active = active;
+  L.steps = c->p.cheb_steps;
+  L.lmin = space == 2 ? Q2_LMIN : Q1_LMIN;
+  L.lmax = space == 2 ? Q2_LMAX : Q1_LMAX;
+  L.space = space;
+  launch_cheb<T>(L, c->st);
+}
+
+template <class T>
+void Engine<T>::block_matvec(const BlkCoef* coef, const cpx<T>* X, cpx<T>* Out, const int* active) {
+  BlkArgs<T> a{};
+  a.tabs = tabs;
+  a.s = c->s;
+  a.J = c->J;
+  a.nu = c->p.nu;
+  a.conv = c->conv;
+  a.coef = coef;
+  a.active = active;
+  a.x = X;
+  a.y = Out;
+  launch_block_matvec<T>(a, c->st);
+}
+
+// P~_j^{-1} (Stokes, Sec. 3.2) or (P~_j^(UZ))^{-1} (Oseen, Algorithm 3) for
+// every frequency: U -> Out.  U and Out must not overlap; T1..T3 are scratch.
+template <class T>
+void Engine<T>::block_prec(const cpx<T>* U, cpx<T>* Out, const int* active) {
+  const int J = c->J;
+  const Slots& s = c->s;
+  cudaStream_t st = c->st;
+  if (!c->oseen) {
+    // W_j^{-1} on the four velocity fields (v and lambda blocks)
+    mg(2, false, c->j_W4, 4 * J, Out, U, active);
+    // S^_j^{-1} = (1 + c1) K_p^{-1} + nu c2 M_p^{-1} on the p and mu blocks
+    mg(1, false, c->j_Kp2, 2 * J, T1, U, active);
+    cheb(1, c->j_Mp2, 2 * J, T2, U, active);
+    launch_lincomb<T>(J, s.nblk, s.nq, Out, s.p, T1, s.p, c->d_sa, T2, s.p, c->d_sb, active, st);
+    launch_lincomb<T>(J, s.nblk, s.nq, Out, s.mu, T1, s.mu, c->d_sa, T2, s.mu, c->d_sb, active, st);
+    return;
+  }
+  // ---- Oseen: Uzawa (Eq. Uzawa11) on G^(1,1), x^(0) = 0
+  cudaMemsetAsync(Out, 0, sizeof(cpx<T>) * (size_t)J * s.nblk, st);
+  const long long lenv = 2LL * s.ns;
+  ComboArgs<T> ca{};
+  ca.tabs = tabs;
+  ca.s = s;
+  ca.J = J;
+  ca.active = active;
+  ca.conv = c->conv;
+  ca.space = 2;
+  for (int step = 0; step < c->p.uzawa_steps; ++step) {
+    // T1[v] = b1 - tau M x1 - (d M + tau L)^H x2
+    ca.nrows = 2;
+    ca.ncoef = 3;
+    ca.coef = c->d_cuza;
+    ca.rows[0] = ComboRow{s.vx, s.vx, {s.vx, s.lx}, 0, {1, 2}, 2, 1};
+    ca.rows[1] = ComboRow{s.vy, s.vy, {s.vy, s.ly}, 0, {1, 2}, 2, 1};
+    ca.x = Out;
+    ca.z = U;
+    ca.out = T1;
+    launch_combo<T>(ca, st);
+    // x1 += (1/tau) M^-1 T1[v]   (M^ = Chebyshev)
+    cheb(2, c->j_M2, 2 * J, T2, T1, active);
+    launch_lincomb<T>(J, s.nblk, lenv, Out, s.vx, Out, s.vx, c->d_one, T2, s.vx, c->d_invtau, active, st);
+    // T1[lam] = b2 - (d M + tau L) x1 + tau/beta M x2
+    ca.coef = c->d_cuzd;
+    ca.rows[0] = ComboRow{s.lx, s.lx, {s.vx, s.lx}, 0, {1, 2}, 2, 1};
+    ca.rows[1] = ComboRow{s.ly, s.ly, {s.vy, s.ly}, 0, {1, 2}, 2, 1};
+    ca.x = Out;
+    ca.z = U;
+    ca.out = T1;
+    launch_combo<T>(ca, st);
+    // S^^{-1} = tau Q^{-H} M Q^{-1}
+    mg(2, c->conv, c->j_Q2, 2 * J, T2, T1, active);
+    ca.coef = c->d_cmass;
+    ca.ncoef = 2;
+    ca.rows[0] = ComboRow{s.lx, 0, {s.lx, 0}, 0, {1, 0}, 1, 0};
+    ca.rows[1] = ComboRow{s.ly, 0, {s.ly, 0}, 0, {1, 0}, 1, 0};
+    ca.x = T2;
+    ca.z = nullptr;
+    ca.out = T3;
+    launch_combo<T>(ca, st);
+    mg(2, c->conv, c->j_QH2, 2 * J, T1, T3, active);
+    // x2 -= (1/mu) tau Q^{-H} M Q^{-1} (...)
+    launch_lincomb<T>(J, s.nblk, lenv, Out, s.lx, Out, s.lx, c->d_one, T1, s.lx, c->d_mtaumu, active, st);
+  }
+  // ---- Algorithm 3: y34 = -S^_j^{-1} (r34 - tau (B y2; B y1))
+  BResArgs<T> br{};
+  br.tabs = tabs;
+  br.s = s;
+  br.J = J;
+  br.c = -c->p.tau;
+  br.out0 = s.p;
+  br.z0 = s.p;
+  br.vel0 = s.lx;
+  br.out1 = s.mu;
+  br.z1 = s.mu;
+  br.vel1 = s.vx;
+  br.active = active;
+  br.x = Out;
+  br.z = U;
+  br.out = T1;
+  launch_bres<T>(br, st);
+  // swap + (tau M_p)^{-1}: T2[p] = Cheb(T1[mu]), T2[mu] = Cheb(T1[p]) (1/tau folded below)
+  cheb(1, c->j_Mp2s, 2 * J, T2, T1, active);
+  // X_p, the second swap's sign and the 1/tau factors
+  ComboArgs<T> cq{};
+  cq.tabs = tabs;
+  cq.s = s;
+  cq.J = J;
+  cq.active = active;
+  cq.conv = c->conv;
+  cq.space = 1;
+  cq.nrows = 2;
+  cq.ncoef = 5;
+  cq.coef = c->d_cxp;
+  cq.rows[0] = ComboRow{s.p, 0, {s.p, s.mu}, 0, {1, 2}, 2, 0};
+  cq.rows[1] = ComboRow{s.mu, 0, {s.p, s.mu}, 0, {3, 4}, 2, 0};
+  cq.x = T2;
+  cq.z = nullptr;
+  cq.out = T3;
+  launch_combo<T>(cq, st);
+  // swap + (tau K_p)^{-1}: Out[p] = MG(T3[mu]), Out[mu] = MG(T3[p])
+  mg(1, false, c->j_Kp2s, 2 * J, Out, T3, active);
+}
+
+// Inner solve on all frequencies: GMRES(A_j, P_j, S_j, eps) or, for the
+// linear variant (Algorithm 1), one application of the block preconditioner.
+template <class T>
+void Engine<T>::inner_solve(const cpx<T>* S, cpx<T>* X, int* its_host) {
+  const int J = c->J;
+  const long long nb = c->s.nblk;
+  cudaStream_t st = c->st;
+  if (c->p.linear) {
+    block_prec(S, X, nullptr);
+    if (its_host)
+      for (int j = 0; j < J; ++j) its_host[j] = 0;
+    return;
+  }
+  GmresState& G = c->gs;
+  const int m = G.m;
+  const long long hs = (long long)(m + 1) * m * 2;  // H stride per frequency (doubles)
+  const size_t vs = (size_t)J * nb;                 // one basis vector (all frequencies)
+  launch_bdot<T>(J, nb, S, S, nb, nb, G.partial, G.g, (long long)(m + 1) * 2, nullptr, false, st);
+  launch_gmres_start(G, st);
+  launch_bscale_inv<T>(J, nb, S, V, nb, G.beta0, 1, G.active, st);
+  for (int i = 0; i < m; ++i) {
+    cpx<T>* Vi = V + (size_t)i * vs;
+    cpx<T>* Zi = Z + (size_t)i * vs;
+    cpx<T>* Vn = V + (size_t)(i + 1) * vs;
+    block_prec(Vi, Zi, G.active);
+    block_matvec(c->d_blkZ, Zi, Vn, G.active);
+    for (int l = 0; l <= i; ++l) {
+      double* h = G.H + ((size_t)l * m + i) * 2;
+      launch_bdot<T>(J, nb, V + (size_t)l * vs, Vn, nb, nb, G.partial, h, hs, G.active, false, st);
+      launch_baxpy_dev<T>(J, nb, V + (size_t)l * vs, Vn, nb, h, hs, 1.0, G.active, st);
+    }
+    double* hn = G.H + ((size_t)(i + 1) * m + i) * 2;
+    launch_bdot<T>(J, nb, Vn, Vn, nb, nb, G.partial, hn, hs, G.active, true, st);
+    launch_bscale_inv<T>(J, nb, Vn, Vn, nb, hn, hs, G.active, st);
+    launch_gmres_givens(G, i, c->p.inner_tol, c->p.fixed_inner_its, st);
+    cudaMemcpyAsync(c->h_count, G.count, sizeof(int), cudaMemcpyDeviceToHost, st);
+    cudaStreamSynchronize(st);
+    if (*c->h_count == 0) break;
+  }
+  launch_gmres_finish<T>(G, nb, Z, (long long)vs, X, st);
+  if (its_host) {
+    cudaMemcpyAsync(its_host, G.its, sizeof(int) * J, cudaMemcpyDeviceToHost, st);
+    cudaStreamSynchronize(st);
+  }
+}
+
+template <class T>
+void Engine<T>::freq_solve(cpx<T>* Rin, cpx<T>* Out, int* its_host) {
+  if (!c->oseen) {
+    launch_stokes_transform<T>(0, c->J, c->s, c->d_tc, Rin, c->st);
+    inner_solve(Rin, Out, its_host);
+    launch_stokes_transform<T>(1, c->J, c->s, c->d_tc, Out, c->st);
+  } else {
+    inner_solve(Rin, Out, its_host);
+  }
+}
+
+template <class T>
+void Engine<T>::apply(const double* r, double* z, int* its_host) {
+  launch_dft_forward<T>(c->K, c->J, c->s.nblk, r, R, cosk, sink, c->st);
+  freq_solve(R, Y, its_host);
+  launch_dft_inverse<T>(c->K, c->J, c->s.nblk, Y, z, cosk, sink, c->st);
+}
+
+// ============================================================================
+// setup
+// ============================================================================
+namespace {
+
+bool valid_params(const pint_params* p, std::string& why) {
+  if (!p) return why = "null params", false;
+  if (p->kind != PINT_STOKES && p->kind != PINT_OSEEN) return why = "kind must be PINT_STOKES or PINT_OSEEN", false;
+  if (p->level < 1 || p->level > 10) return why = "level must be in [1, 10]", false;
+  if (!(p->x1 > p->x0)) return why = "x1 must exceed x0", false;
+  if (p->n_t < 1 || p->n_t > 4096) return why = "n_t must be in [1, 4096]", false;
+  if (!(p->tau > 0) || !(p->beta > 0) || !(p->nu > 0)) return why = "tau, beta, nu must be positive", false;
+  if (p->wind != PINT_WIND_NONE && p->wind != PINT_WIND_RECIRC) return why = "unknown wind", false;
+  if (p->wind == PINT_WIND_RECIRC && (p->x0 != -1.0 || p->x1 != 1.0))
+    return why = "the recirculating wind requires the domain [-1,1]^2", false;
+  if (p->prec != PINT_PREC_FP64 && p->prec != PINT_PREC_FP32) return why = "unknown precision", false;
+  if (p->outer_restart < 1 || p->outer_restart > 200) return why = "outer_restart must be in [1, 200]", false;
+  if (p->outer_maxit < 1) return why = "outer_maxit must be positive", false;
+  if (!(p->outer_tol > 0)) return why = "outer_tol must be positive", false;
+  if (p->inner_maxit < 1 || p->inner_maxit > 1000) return why = "inner_maxit must be in [1, 1000]", false;
+  if (p->fixed_inner_its < 0 || p->fixed_inner_its > 1000) return why = "fixed_inner_its out of range", false;
+  if (!(p->inner_tol >= 0)) return why = "inner_tol must be >= 0", false;
+  if (p->mg_cycles < 1 || p->mg_pre < 0 || p->mg_post < 0 || p->cheb_steps < 1 || p->uzawa_steps < 1)
+    return why = "multigrid / Chebyshev / Uzawa counts must be positive", false;
+  if (!(p->uzawa_mu > 0) || !(p->sor_omega > 0) || !(p->sor_omega < 2))
+    return why = "uzawa_mu must be positive and sor_omega in (0, 2)", false;
+  return true;
+}
+
+inline std::vector<double> cplx_table(int J, double re, double im) {
+  std::vector<double> v(2 * (size_t)J);
+  for (int j = 0; j < J; ++j) {
+    v[2 * j] = re;
+    v[2 * j + 1] = im;
+  }
+  return v;
+}
+
+template <class T>
+bool setup_engine(pint_ctx* c, Engine<T>& e, size_t mg_jobs_q2, size_t mg_jobs_q1, size_t cheb_jobs_q2,
+                  size_t cheb_jobs_q1) {
+  e.c = c;
+  e.tabs = tabs_of<T>(c);
+  const size_t fv = (size_t)c->J * c->s.nblk;
+  if (!c->alloc(&e.R, fv * sizeof(cpx<T>)) || !c->alloc(&e.Y, fv * sizeof(cpx<T>)) ||
+      !c->alloc(&e.T1, fv * sizeof(cpx<T>)) || !c->alloc(&e.T2, fv * sizeof(cpx<T>)) ||
+      !c->alloc(&e.T3, fv * sizeof(cpx<T>)))
+    return false;
+  if (!c->p.linear) {
+    const int m = c->m_in;
+    if (!c->alloc(&e.V, (size_t)(m + 1) * fv * sizeof(cpx<T>)) || !c->alloc(&e.Z, (size_t)m * fv * sizeof(cpx<T>)))
+      return false;
+  }
+  const size_t mgws = std::max(mg_jobs_q2 * (size_t)c->lay2.per_job, mg_jobs_q1 * (size_t)c->lay1.per_job);
+  const size_t chws = std::max(cheb_jobs_q2 * (size_t)c->cheb_per_q2, cheb_jobs_q1 * (size_t)c->cheb_per_q1);
+  if (!c->alloc(&e.mgws, mgws * sizeof(cpx<T>)) || !c->alloc(&e.chebws, chws * sizeof(cpx<T>))) return false;
+  std::vector<T> cs(c->K), sn(c->K);
+  for (int k = 0; k < c->K; ++k) {
+    const double a = 2.0 * M_PI * (double)k / (double)c->K;
+    cs[k] = (T)std::cos(a);
+    sn[k] = (T)std::sin(a);
+  }
+  return c->upload(&e.cosk, cs) && c->upload(&e.sink, sn);
+}
+
+MGLayout make_layout(int nlev, int N, int space) {
+  MGLayout L{};
+  L.nlev = nlev;
+  long long off = 0;
+  for (int l = 0; l < nlev; ++l) {
+    const int Nl = N >> l;
+    L.n[l] = space == 2 ? 2 * Nl + 1 : Nl + 1;
+  }
+  for (int l = 1; l < nlev; ++l) {
+    const long long sz = (long long)L.n[l] * L.n[l];
+    L.off_x[l] = off;
+    off += sz;
+    L.off_b[l] = off;
+    off += sz;
+  }
+  for (int l = 0; l + 1 < nlev; ++l) {
+    L.off_r[l] = off;
+    off += (long long)L.n[l] * L.n[l];
+  }
+  L.per_job = off > 0 ? off : 1;
+  return L;
+}
+
+pint_status build(pint_ctx* c) {
+  const pint_params& p = c->p;
+  c->N = 1 << p.level;
+  c->K = p.n_t;
+  c->J = p.n_t / 2 + 1;
+  c->nlev = p.level;  // grids N, N/2, ..., 2
+  c->oseen = p.kind == PINT_OSEEN;
+  c->conv = p.wind == PINT_WIND_RECIRC;
+  c->fp32 = p.prec == PINT_PREC_FP32;
+  c->m_in = p.fixed_inner_its > 0 ? p.fixed_inner_its : p.inner_maxit;
+  const int N = c->N, J = c->J;
+  Slots& s = c->s;
+  s.n2 = 2 * N + 1;
+  s.n1 = N + 1;
+  s.ns = s.n2 * s.n2;
+  s.nq = s.n1 * s.n1;
+  s.vx = 0;
+  s.vy = s.ns;
+  s.p = 2LL * s.ns;
+  s.lx = 2LL * s.ns + s.nq;
+  s.ly = 3LL * s.ns + s.nq;
+  s.mu = 4LL * s.ns + s.nq;
+  s.nblk = 4LL * s.ns + 2LL * s.nq;
+
+  if (!c->cu(cudaStreamSynchronize(c->st), "stream check")) return PINT_ERR_CUDA;
+
+  // ---- 1-D band tables per level, FP64 and FP32
+  c->t64.nlev = c->t32.nlev = c->nlev;
+  for (int l = 0; l < c->nlev; ++l) {
+    const int Nl = N >> l;
+    std::vector<double> q2, q1;
+    build_level_tables(Nl, p.x0, p.x1, q2, q1);
+    std::vector<float> q2f(q2.begin(), q2.end()), q1f(q1.begin(), q1.end());
+    double *d2, *d1;
+    float *f2, *f1;
+    if (!c->upload(&d2, q2) || !c->upload(&d1, q1) || !c->upload(&f2, q2f) || !c->upload(&f1, q1f))
+      return c->fail(PINT_ERR_OOM, "device allocation failed (tables)");
+    c->t64.N[l] = c->t32.N[l] = Nl;
+    c->t64.q2[l] = d2;
+    c->t64.q1[l] = d1;
+    c->t32.q2[l] = f2;
+    c->t32.q1[l] = f1;
+  }
+  {
+    std::vector<double> bt;
+    build_b_tables(N, p.x0, p.x1, bt);
+    std::vector<float> btf(bt.begin(), bt.end());
+    double* d;
+    float* f;
+    if (!c->upload(&d, bt) || !c->upload(&f, btf)) return c->fail(PINT_ERR_OOM, "device allocation failed (B)");
+    c->t64.bt = d;
+    c->t32.bt = f;
+  }
+
+  // ---- per-frequency constants (Sec. 3.1-3.2, Sec. 4)
+  const double tau = p.tau, beta = p.beta, nu = p.nu, mu = p.uzawa_mu;
+  std::vector<double> dr(J), dc(J), c1(J), c2(J);
+  for (int j = 0; j < J; ++j) {
+    const double th = 2.0 * M_PI * (double)j / (double)c->K;
+    dr[j] = 1.0 - std::cos(th);  // d_j = 1 - exp(-2 pi i j / K)
+    dc[j] = std::sin(th);
+    c1[j] = dr[j] / std::sqrt(tau * tau / beta + dc[j] * dc[j]);
+    c2[j] = 1.0 / std::sqrt(1.0 / beta + dc[j] * dc[j] / (tau * tau));
+  }
+  // operators: [0, J): W_j (Stokes) / Q_j (Oseen); [J, 2J): Q_j^H; 2J: K_p; 2J+1: M; 2J+2: M_p
+  c->nops = 2 * J + 3;
+  std::vector<OpCoef> ops(c->nops, OpCoef{0, 0, 0, 0});
+  std::vector<int> space(c->nops, 0), convf(c->nops, 0);
+  const double sb = 1.0 / std::sqrt(beta);
+  for (int j = 0; j < J; ++j) {
+    if (!c->oseen) {
+      ops[j] = OpCoef{1.0 + c1[j], 0.0, c2[j] * nu, 0.0};  // W_j = (1 + c1) M + c2 nu K
+      space[j] = 2;
+    } else {
+      // Q_j = d_j M + tau (nu K + N) + tau/sqrt(beta) M ; Q_j^H with N^T = -N
+      ops[j] = OpCoef{dr[j] + tau * sb, -dc[j], tau * nu, tau};
+      ops[J + j] = OpCoef{dr[j] + tau * sb, dc[j], tau * nu, -tau};
+      space[j] = space[J + j] = 2;
+      convf[j] = convf[J + j] = c->conv ? 1 : 0;
+    }
+  }
+  ops[2 * J] = OpCoef{0.0, 0.0, 1.0, 0.0};
+  space[2 * J] = 1;
+  ops[2 * J + 1] = OpCoef{1.0, 0.0, 0.0, 0.0};
+  ops[2 * J + 2] = OpCoef{1.0, 0.0, 0.0, 0.0};
+  int *d_space, *d_conv, *d_status;
+  if (!c->upload(&c->d_ops, ops) || !c->upload(&d_space, space) || !c->upload(&d_conv, convf) ||
+      !c->alloc(&d_status, sizeof(int) * c->nops) ||
+      !c->alloc(&c->d_cinv, sizeof(double) * 2 * PINT_NC_MAX * PINT_NC_MAX * c->nops))
+    return c->fail(PINT_ERR_OOM, "device allocation failed (operators)");
+  cudaMemsetAsync(d_status, 0, sizeof(int) * c->nops, c->st);
+  launch_coarse_setup(c->t64, c->d_ops, d_space, d_conv, c->nops, c->d_cinv, d_status, c->st);
+  if (!c->launched("coarse setup")) return PINT_ERR_CUDA;
+  {
+    std::vector<int> st_h(c->nops);
+    if (!c->cu(cudaMemcpyAsync(st_h.data(), d_status, sizeof(int) * c->nops, cudaMemcpyDeviceToHost, c->st),
+               "coarse status") ||
+        !c->cu(cudaStreamSynchronize(c->st), "coarse setup"))
+      return PINT_ERR_CUDA;
+    for (int o = 0; o < c->nops; ++o)
+      if (st_h[o] != 0) return c->fail(PINT_ERR_ARG, "coarse-grid operator is singular or too large");
+  }
+
+  // frequency-block coefficients: G_j (Eq. SubBlockG) and Z_j (Eq. GJTransformation)
+  std::vector<BlkCoef> bz(J), bg(J);
+  for (int j = 0; j < J; ++j) {
+    bg[j] = BlkCoef{tau, 0, dr[j], dc[j], dr[j], -dc[j], -tau / beta, 0, tau, tau, tau, 0};
+    bz[j] = c->oseen ? bg[j] : BlkCoef{1, 0, c1[j], 0, c1[j], 0, -1, 0, c2[j], c2[j], 1, 0};
+  }
+  std::vector<double> tc(3 * (size_t)J), sa(2 * (size_t)J), sbv(2 * (size_t)J);
+  for (int j = 0; j < J; ++j) {
+    tc[3 * j] = std::sqrt(tau);
+    tc[3 * j + 1] = dc[j];
+    tc[3 * j + 2] = c2[j];
+    sa[2 * j] = 1.0 + c1[j];
+    sa[2 * j + 1] = 0;
+    sbv[2 * j] = nu * c2[j];
+    sbv[2 * j + 1] = 0;
+  }
+  // Oseen combination coefficients (per frequency)
+  std::vector<OpCoef> cuza(3 * (size_t)J), cuzd(3 * (size_t)J), cmass(2 * (size_t)J), cxp(5 * (size_t)J);
+  for (int j = 0; j < J; ++j) {
+    // T1[v] = 1 b1 + (-tau M) x1 + (-(conj d) M - tau nu K + tau N) x2
+    cuza[3 * j + 0] = OpCoef{1, 0, 0, 0};
+    cuza[3 * j + 1] = OpCoef{-tau, 0, 0, 0};
+    cuza[3 * j + 2] = OpCoef{-dr[j], -dc[j], -tau * nu, tau};
+    // T1[lam] = 1 b2 + (-d M - tau nu K - tau N) x1 + (tau/beta M) x2
+    cuzd[3 * j + 0] = OpCoef{1, 0, 0, 0};
+    cuzd[3 * j + 1] = OpCoef{-dr[j], dc[j], -tau * nu, -tau};
+    cuzd[3 * j + 2] = OpCoef{tau / beta, 0, 0, 0};
+    cmass[2 * j + 0] = OpCoef{0, 0, 0, 0};
+    cmass[2 * j + 1] = OpCoef{1, 0, 0, 0};
+    // T3[p] = -(1/tau^2) [tau M_p a + (conj(d) M_p + tau nu K_p - tau N_p) b]
+    // T3[mu] = -(1/tau^2) [(d M_p + tau nu K_p + tau N_p) a - tau/beta M_p b]
+    const double it2 = 1.0 / (tau * tau);
+    cxp[5 * j + 0] = OpCoef{0, 0, 0, 0};
+    cxp[5 * j + 1] = OpCoef{-1.0 / tau, 0, 0, 0};
+    cxp[5 * j + 2] = OpCoef{-dr[j] * it2, dc[j] * it2, -nu / tau, 1.0 / tau};
+    cxp[5 * j + 3] = OpCoef{-dr[j] * it2, -dc[j] * it2, -nu / tau, -1.0 / tau};
+    cxp[5 * j + 4] = OpCoef{1.0 / (beta * tau), 0, 0, 0};
+  }
+  if (!c->upload(&c->d_blkZ, bz) || !c->upload(&c->d_blkG, bg) || !c->upload(&c->d_tc, tc) ||
+      !c->upload(&c->d_sa, sa) || !c->upload(&c->d_sb, sbv) || !c->upload(&c->d_one, cplx_table(J, 1, 0)) ||
+      !c->upload(&c->d_invtau, cplx_table(J, 1.0 / tau, 0)) ||
+      !c->upload(&c->d_mtaumu, cplx_table(J, -tau / mu, 0)) || !c->upload(&c->d_cuza, cuza) ||
+      !c->upload(&c->d_cuzd, cuzd) || !c->upload(&c->d_cmass, cmass) || !c->upload(&c->d_cxp, cxp))
+    return c->fail(PINT_ERR_OOM, "device allocation failed (coefficients)");
+
+  // ---- job tables
+  auto jobs = [&](std::initializer_list<std::pair<long long, long long>> sl, int opbase, bool per_j_op) {
+    std::vector<FieldJob> v;
+    for (int j = 0; j < J; ++j)
+      for (auto& xb : sl)
+        v.push_back(FieldJob{(long long)j * s.nblk + xb.first, (long long)j * s.nblk + xb.second,
+                             per_j_op ? opbase + j : opbase, j});
+    return v;
+  };
+  bool ok = true;
+  if (!c->oseen) {
+    ok = ok && c->upload(&c->j_W4, jobs({{s.vx, s.vx}, {s.vy, s.vy}, {s.lx, s.lx}, {s.ly, s.ly}}, 0, true));
+    ok = ok && c->upload(&c->j_Kp2, jobs({{s.p, s.p}, {s.mu, s.mu}}, 2 * J, false));
+    ok = ok && c->upload(&c->j_Mp2, jobs({{s.p, s.p}, {s.mu, s.mu}}, 2 * J + 2, false));
+  } else {
+    ok = ok && c->upload(&c->j_Q2, jobs({{s.lx, s.lx}, {s.ly, s.ly}}, 0, true));
+    ok = ok && c->upload(&c->j_QH2, jobs({{s.lx, s.lx}, {s.ly, s.ly}}, J, true));
+    ok = ok && c->upload(&c->j_M2, jobs({{s.vx, s.vx}, {s.vy, s.vy}}, 2 * J + 1, false));
+    ok = ok && c->upload(&c->j_Kp2s, jobs({{s.p, s.mu}, {s.mu, s.p}}, 2 * J, false));
+    ok = ok && c->upload(&c->j_Mp2s, jobs({{s.p, s.mu}, {s.mu, s.p}}, 2 * J + 2, false));
+  }
+  ok = ok && c->alloc(&c->j_one, sizeof(FieldJob)) && c->alloc(&c->d_active_one, sizeof(int) * J);
+  if (!ok) return c->fail(PINT_ERR_OOM, "device allocation failed (jobs)");
+
+  // ---- multigrid / Chebyshev workspaces
+  c->lay2 = make_layout(c->nlev, N, 2);
+  c->lay1 = make_layout(c->nlev, N, 1);
+  c->cheb_per_q2 = 2LL * s.ns;
+  c->cheb_per_q1 = 2LL * s.nq;
+  const size_t mgq2 = c->oseen ? 2 * (size_t)J : 4 * (size_t)J;
+  const size_t mgq1 = 2 * (size_t)J;
+  const size_t chq2 = c->oseen ? 2 * (size_t)J : 1;
+  const size_t chq1 = 2 * (size_t)J;
+
+  // ---- inner GMRES state
+  if (!p.linear) {
+    GmresState& G = c->gs;
+    G.J = J;
+    G.m = c->m_in;
+    const size_t m = (size_t)c->m_in;
+    ok = c->alloc(&G.H, sizeof(double) * 2 * J * (m + 1) * m) && c->alloc(&G.g, sizeof(double) * 2 * J * (m + 1)) &&
+         c->alloc(&G.cs, sizeof(double) * J * m) && c->alloc(&G.sn, sizeof(double) * 2 * J * m) &&
+         c->alloc(&G.beta0, sizeof(double) * J) && c->alloc(&G.y, sizeof(double) * 2 * J * m) &&
+         c->alloc(&G.partial, sizeof(double) * 2 * J * GM_CH) && c->alloc(&G.active, sizeof(int) * J) &&
+         c->alloc(&G.its, sizeof(int) * J) && c->alloc(&G.count, sizeof(int));
+    if (!ok) return c->fail(PINT_ERR_OOM, "device allocation failed (inner GMRES)");
+  }
+  if (c->fp32)
+    ok = setup_engine<float>(c, c->e32, mgq2, mgq1, chq2, chq1);
+  else
+    ok = setup_engine<double>(c, c->e64, mgq2, mgq1, chq2, chq1);
+  if (!ok) return c->fail(PINT_ERR_OOM, "device allocation failed (preconditioner workspace)");
+
+  // ---- outer FGMRES workspace (FP64)
+  const size_t n = (size_t)c->K * s.nblk;
+  const size_t m = (size_t)p.outer_restart;
+  ok = c->alloc(&c->oV, sizeof(double) * n * (m + 1)) && c->alloc(&c->oZ, sizeof(double) * n * m) &&
+       c->alloc(&c->ob, sizeof(double) * n) && c->alloc(&c->ox, sizeof(double) * n) &&
+       c->alloc(&c->ot, sizeof(double) * n) && c->alloc(&c->opart, sizeof(double) * MDOT_CTAS * 8) &&
+       c->alloc(&c->oh, sizeof(double) * (2 * m + 8)) &&
+       c->alloc(&c->ofreq, sizeof(double) * 2 * (size_t)J * s.nblk);
+  if (!ok) return c->fail(PINT_ERR_OOM, "device allocation failed (outer FGMRES)");
+  if (!c->cu(cudaMallocHost(&c->h_pinned, sizeof(double) * (2 * m + 8)), "pinned host buffer") ||
+      !c->cu(cudaMallocHost(&c->h_count, sizeof(int)), "pinned host buffer"))
+    return PINT_ERR_OOM;
+  if (!c->cu(cudaStreamSynchronize(c->st), "setup")) return PINT_ERR_CUDA;
+  return PINT_OK;
+}
+
+void free_ctx(pint_ctx* c) {
+  if (!c) return;
+  if (c->st) cudaStreamSynchronize(c->st);
+  for (void* v : c->allocs) cudaFree(v);
+  if (c->h_pinned) cudaFreeHost(c->h_pinned);
+  if (c->h_count) cudaFreeHost(c->h_count);
+  delete c;
+}
+
+// ---------------------------------------------------------------- wrappers
+void kkt(pint_ctx* c, const double* x, double* y) {
+  KKTArgs a{};
+  a.tabs = c->t64;
+  a.s = c->s;
+  a.K = c->K;
+  a.tau = c->p.tau;
+  a.beta = c->p.beta;
+  a.nu = c->p.nu;
+  a.conv = c->conv;
+  a.x = x;
+  a.y = y;
+  launch_kkt_matvec(a, c->st);
+}
+
+void apply_prec(pint_ctx* c, const double* r, double* z, int* its) {
+  if (c->fp32)
+    c->e32.apply(r, z, its);
+  else
+    c->e64.apply(r, z, its);
+}
+
+double dot_dev(pint_ctx* c, const double* a, const double* b, long long n) {
+  launch_mdot(a, 1, b, n, c->opart, c->oh, c->st);
+  cudaMemcpyAsync(c->h_pinned, c->oh, sizeof(double), cudaMemcpyDeviceToHost, c->st);
+  cudaStreamSynchronize(c->st);
+  return c->h_pinned[0];
+}
+
+// Outer FP64 FGMRES(m) with classical Gram-Schmidt + reorthogonalisation.
+pint_status fgmres(pint_ctx* c, double* x, pint_solve_info* info) {
+  const long long n = (long long)c->K * c->s.nblk;
+  const int m = c->p.outer_restart;
+  cudaStream_t st = c->st;
+  pint_solve_info inf{};
+  const auto t0 = std::chrono::steady_clock::now();
+  double t_prec = 0, t_mv = 0, t_orth = 0;
+  auto now = [] { return std::chrono::steady_clock::now(); };
+  auto ms = [](std::chrono::steady_clock::time_point a, std::chrono::steady_clock::time_point b) {
+    return std::chrono::duration<double, std::milli>(b - a).count();
+  };
+  std::vector<int> its(c->J, 0);
+  const double bnorm = std::sqrt(dot_dev(c, c->ob, c->ob, n));
+  if (bnorm == 0.0) {
+    cudaMemsetAsync(x, 0, sizeof(double) * n, st);
+    cudaStreamSynchronize(st);
+    if (info) *info = inf;
+    return PINT_OK;
+  }
+  // r = b - A x
+  kkt(c, x, c->ot);
+  launch_axpby(1.0, c->ob, -1.0, c->ot, n, st);
+  double beta = std::sqrt(dot_dev(c, c->ot, c->ot, n));
+  double relres = beta / bnorm;
+  int total = 0;
+  std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), y(m);
+  while (total < c->p.outer_maxit && relres > c->p.outer_tol) {
+    launch_axpby(1.0 / beta, c->ot, 0.0, c->oV, n, st);
+    std::fill(g.begin(), g.end(), 0.0);
+    g[0] = beta;
+    int k = 0;
+    for (int i = 0; i < m; ++i) {
+      double* Vi = c->oV + (size_t)i * n;
+      double* Zi = c->oZ + (size_t)i * n;
+      double* Vn = c->oV + (size_t)(i + 1) * n;
+      auto a0 = now();
+      apply_prec(c, Vi, Zi, its.data());
+      cudaStreamSynchronize(st);
+      auto a1 = now();
+      for (int j = 0; j < c->J; ++j) {
+        inf.inner_iterations_total += its[j];
+        inf.inner_iterations_max = std::max(inf.inner_iterations_max, its[j]);
+      }
+      inf.precond_applies++;
+      kkt(c, Zi, Vn);
+      cudaStreamSynchronize(st);
+      auto a2 = now();
+      // CGS2
+      launch_mdot(c->oV, i + 1, Vn, n, c->opart, c->oh, st);
+      launch_maxpy(c->oV, i + 1, c->oh, Vn, n, st);
+      launch_mdot(c->oV, i + 1, Vn, n, c->opart, c->oh + (i + 1), st);
+      launch_maxpy(c->oV, i + 1, c->oh + (i + 1), Vn, n, st);
+      launch_mdot(Vn, 1, Vn, n, c->opart, c->oh + 2 * (i + 1), st);
+      cudaMemcpyAsync(c->h_pinned, c->oh, sizeof(double) * (2 * (i + 1) + 1), cudaMemcpyDeviceToHost, st);
+      if (!c->cu(cudaStreamSynchronize(st), "FGMRES iteration")) return PINT_ERR_CUDA;
+      const double hn = std::sqrt(std::max(0.0, c->h_pinned[2 * (i + 1)]));
+      for (int l = 0; l <= i; ++l) H[(size_t)l * m + i] = c->h_pinned[l] + c->h_pinned[i + 1 + l];
+      H[(size_t)(i + 1) * m + i] = hn;
+      if (hn != 0.0) launch_axpby(1.0 / hn, Vn, 0.0, Vn, n, st);
+      auto a3 = now();
+      t_prec += ms(a0, a1);
+      t_mv += ms(a1, a2);
+      t_orth += ms(a2, a3);
+      for (int l = 0; l < i; ++l) {
+        const double t = cs[l] * H[(size_t)l * m + i] + sn[l] * H[(size_t)(l + 1) * m + i];
+        H[(size_t)(l + 1) * m + i] = -sn[l] * H[(size_t)l * m + i] + cs[l] * H[(size_t)(l + 1) * m + i];
+        H[(size_t)l * m + i] = t;
+      }
+      const double den = std::hypot(H[(size_t)i * m + i], hn);
+      cs[i] = H[(size_t)i * m + i] / den;
+      sn[i] = hn / den;
+      H[(size_t)i * m + i] = den;
+      H[(size_t)(i + 1) * m + i] = 0.0;
+      g[i + 1] = -sn[i] * g[i];
+      g[i] = cs[i] * g[i];
+      ++total;
+      k = i + 1;
+      if (total <= 256) inf.relres_history[total - 1] = std::fabs(g[i + 1]) / bnorm;
+      if (std::fabs(g[i + 1]) <= c->p.outer_tol * bnorm || total >= c->p.outer_maxit || hn == 0.0) break;
+    }
+    for (int l = k - 1; l >= 0; --l) {
+      double sacc = g[l];
+      for (int q = l + 1; q < k; ++q) sacc -= H[(size_t)l * m + q] * y[q];
+      y[l] = sacc / H[(size_t)l * m + l];
+    }
+    for (int l = 0; l < k; ++l) c->h_pinned[l] = -y[l];
+    cudaMemcpyAsync(c->oh, c->h_pinned, sizeof(double) * k, cudaMemcpyHostToDevice, st);
+    launch_maxpy(c->oZ, k, c->oh, x, n, st);  // x += Z y
+    kkt(c, x, c->ot);
+    launch_axpby(1.0, c->ob, -1.0, c->ot, n, st);
+    beta = std::sqrt(dot_dev(c, c->ot, c->ot, n));
+    relres = beta / bnorm;
+    inf.restarts++;
+    if (!c->launched("FGMRES restart")) return PINT_ERR_CUDA;
+  }
+  inf.outer_iterations = total;
+  inf.relres = relres;
+  inf.ms_precond = t_prec;
+  inf.ms_matvec = t_mv;
+  inf.ms_orth = t_orth;
+  inf.ms_total = ms(t0, now());
+  if (info) *info = inf;
+  return relres <= c->p.outer_tol ? PINT_OK : c->fail(PINT_ERR_NOT_CONVERGED, "outer FGMRES did not converge");
+}
+
+}  // namespace
+
+// ============================================================================
+// C ABI
+// ============================================================================
+extern "C" {
+
+void pint_default_params(pint_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->kind = PINT_STOKES;
+  p->level = 3;
+  p->x0 = 0.0;
+  p->x1 = 1.0;
+  p->n_t = 8;
+  p->tau = 1.0 / 9.0;
+  p->beta = 1e-2;
+  p->nu = 1e-2;
+  p->wind = PINT_WIND_NONE;
+  p->prec = PINT_PREC_FP64;
+  p->outer_restart = 30;
+  p->outer_maxit = 300;
+  p->outer_tol = 1e-8;
+  p->inner_tol = 1e-2;
+  p->inner_maxit = 100;
+  p->mg_cycles = 4;
+  p->mg_pre = 2;
+  p->mg_post = 2;
+  p->cheb_steps = 10;
+  p->uzawa_steps = 6;
+  p->uzawa_mu = 0.75;
+  p->sor_omega = 1.0;
+  p->fixed_inner_its = 0;
+  p->linear = 0;
+}
+
+pint_status pint_create(const pint_params* p, void* stream, pint_handle* out) {
+  if (!out) {
+    g_err = "null output handle";
+    return PINT_ERR_ARG;
+  }
+  *out = nullptr;
+  std::string why;
+  if (!valid_params(p, why)) {
+    g_err = why;
+    return PINT_ERR_ARG;
+  }
+  pint_ctx* c = new (std::nothrow) pint_ctx();
+  if (!c) {
+    g_err = "host allocation failed";
+    return PINT_ERR_OOM;
+  }
+  c->p = *p;
+  c->st = static_cast<cudaStream_t>(stream);
+  pint_status s = build(c);
+  if (s != PINT_OK) {
+    std::string m = c->err;
+    free_ctx(c);
+    g_err = m;
+    return s;
+  }
+  *out = c;
+  return PINT_OK;
+}
+
+pint_status pint_destroy(pint_handle h) {
+  free_ctx(h);
+  return PINT_OK;
+}
+
+pint_status pint_get_sizes(pint_handle h, pint_sizes* s) {
+  if (!h || !s) {
+    g_err = "null argument";
+    return PINT_ERR_ARG;
+  }
+  s->N = h->N;
+  s->n_t = h->K;
+  s->J = h->J;
+  s->n_s = (size_t)h->s.ns;
+  s->n_q = (size_t)h->s.nq;
+  s->n_blk = (size_t)h->s.nblk;
+  s->kkt_len = (size_t)h->K * h->s.nblk;
+  s->freq_len = (size_t)h->J * h->s.nblk;
+  s->device_bytes = h->dev_bytes;
+  return PINT_OK;
+}
+
+pint_status pint_set_data(pint_handle h, const double* vd, const double* f, const double* v0) {
+  if (!h) {
+    g_err = "null handle";
+    return PINT_ERR_ARG;
+  }
+  if (!vd) return h->fail(PINT_ERR_ARG, "vd must not be null");
+  const size_t nvd = (size_t)h->K * 2 * h->s.ns, nv0 = 2 * (size_t)h->s.ns;
+  for (size_t i = 0; i < nvd; ++i)
+    if (!std::isfinite(vd[i]) || (f && !std::isfinite(f[i])))
+      return h->fail(PINT_ERR_NONFINITE, "non-finite value in vd or f");
+  if (v0)
+    for (size_t i = 0; i < nv0; ++i)
+      if (!std::isfinite(v0[i])) return h->fail(PINT_ERR_NONFINITE, "non-finite value in v0");
+  double *dvd = nullptr, *df = nullptr, *dv0 = nullptr;
+  bool ok = cudaMalloc(&dvd, sizeof(double) * nvd) == cudaSuccess;
+  if (ok && f) ok = cudaMalloc(&df, sizeof(double) * nvd) == cudaSuccess;
+  if (ok && v0) ok = cudaMalloc(&dv0, sizeof(double) * nv0) == cudaSuccess;
+  pint_status rc = PINT_OK;
+  if (!ok) {
+    cudaGetLastError();
+    rc = h->fail(PINT_ERR_OOM, "device allocation failed (data)");
+  } else {
+    ok = h->cu(cudaMemcpy(dvd, vd, sizeof(double) * nvd, cudaMemcpyHostToDevice), "upload vd");
+    if (ok && f) ok = h->cu(cudaMemcpy(df, f, sizeof(double) * nvd, cudaMemcpyHostToDevice), "upload f");
+    if (ok && v0) ok = h->cu(cudaMemcpy(dv0, v0, sizeof(double) * nv0, cudaMemcpyHostToDevice), "upload v0");
+    if (ok) {
+      RhsArgs a{};
+      a.tabs = h->t64;
+      a.s = h->s;
+      a.K = h->K;
+      a.tau = h->p.tau;
+      a.vd = dvd;
+      a.f = df;
+      a.v0 = dv0;
+      a.b = h->ob;
+      launch_rhs(a, h->st);
+      ok = h->launched("rhs") && h->cu(cudaStreamSynchronize(h->st), "rhs");
+    }
+    if (!ok) rc = PINT_ERR_CUDA;
+  }
+  cudaFree(dvd);
+  if (df) cudaFree(df);
+  if (dv0) cudaFree(dv0);
+  if (rc == PINT_OK) h->have_data = true;
+  return rc;
+}
+
+pint_status pint_get_rhs(pint_handle h, double* b_dev) {
+  if (!h || !b_dev) {
+    g_err = "null argument";
+    return PINT_ERR_ARG;
+  }
+  if (!h->have_data) return h->fail(PINT_ERR_STATE, "pint_set_data has not been called");
+  const size_t n = (size_t)h->K * h->s.nblk;
+  if (!h->cu(cudaMemcpyAsync(b_dev, h->ob, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->st), "copy rhs"))
+    return PINT_ERR_CUDA;
+  return PINT_OK;
+}
+
+pint_status pint_kkt_matvec(pint_handle h, const double* x, double* y) {
+  if (!h || !x || !y) {
+    g_err = "null argument";
+    return PINT_ERR_ARG;
+  }
+  const size_t n = (size_t)h->K * h->s.nblk;
+  if (!h->cu(cudaMemcpyAsync(h->ox, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->st), "copy x"))
+    return PINT_ERR_CUDA;
+  launch_mask_blocks(h->s, h->K, 1, h->ox, h->st);
+  kkt(h, h->ox, y);
+  return h->launched("kkt matvec") ? PINT_OK : PINT_ERR_CUDA;
+}
+
+pint_status pint_apply_preconditioner(pint_handle h, const double* r, double* z) {
+  if (!h || !r || !z) {
+    g_err = "null argument";
+    return PINT_ERR_ARG;
+  }
+  const size_t n = (size_t)h->K * h->s.nblk;
+  if (!h->cu(cudaMemcpyAsync(h->ot, r, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->st), "copy r"))
+    return PINT_ERR_CUDA;
+  launch_mask_blocks(h->s, h->K, 1, h->ot, h->st);
+  apply_prec(h, h->ot, z, nullptr);
+  return h->launched("preconditioner") ? PINT_OK : PINT_ERR_CUDA;
+}
+
+pint_status pint_solve(pint_handle h, double* x, pint_solve_info* info) {
+  if (!h || !x) {
+    g_err = "null argument";
+    return PINT_ERR_ARG;
+  }
+  if (!h->have_data) return h->fail(PINT_ERR_STATE, "pint_set_data has not been called");
+  const size_t n = (size_t)h->K * h->s.nblk;
+  if (!h->cu(cudaMemcpyAsync(h->ox, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->st), "copy x0"))
+    return PINT_ERR_CUDA;
+  launch_mask_blocks(h->s, h->K, 1, h->ox, h->st);
+  pint_status rc = fgmres(h, h->ox, info);
+  if (!h->cu(cudaMemcpyAsync(x, h->ox, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->st), "copy x") ||
+      !h->cu(cudaStreamSynchronize(h->st), "solve"))
+    return PINT_ERR_CUDA;
+  return rc;
+}
+
+pint_status pint_solve_host(pint_handle h, double* x_host, pint_solve_info* info) {
+  if (!h || !x_host) {
+    g_err = "null argument";
+    return PINT_ERR_ARG;
+  }
+  if (!h->have_data) return h->fail(PINT_ERR_STATE, "pint_set_data has not been called");
+  const size_t n = (size_t)h->K * h->s.nblk;
+  if (!h->cu(cudaMemcpyAsync(h->ox, x_host, sizeof(double) * n, cudaMemcpyHostToDevice, h->st), "upload x0"))
+    return PINT_ERR_CUDA;
+  launch_mask_blocks(h->s, h->K, 1, h->ox, h->st);
+  pint_status rc = fgmres(h, h->ox, info);
+  if (!h->cu(cudaMemcpyAsync(x_host, h->ox, sizeof(double) * n, cudaMemcpyDeviceToHost, h->st), "download x") ||
+      !h->cu(cudaStreamSynchronize(h->st), "solve"))
+    return PINT_ERR_CUDA;
+  return rc;
+}
+
+}  // extern "C"
+
+// -------------------------------------------------------- component entries
+namespace {
+template <class T>
+void to_T(pint_ctx* c, const double* src, cpx<T>* dst, size_t ncplx);
+template <>
+void to_T<double>(pint_ctx* c, const double* src, cpx<double>* dst, size_t n) {
+  cudaMemcpyAsync(dst, src, sizeof(double) * 2 * n, cudaMemcpyDeviceToDevice, c->st);
+}
+template <>
+void to_T<float>(pint_ctx* c, const double* src, cpx<float>* dst, size_t n) {
+  launch_copy_d2f(src, reinterpret_cast<float*>(dst), (long long)(2 * n), c->st);
+}
+template <class T>
+void from_T(pint_ctx* c, const cpx<T>* src, double* dst, size_t ncplx);
+template <>
+void from_T<double>(pint_ctx* c, const cpx<double>* src, double* dst, size_t n) {
+  cudaMemcpyAsync(dst, src, sizeof(double) * 2 * n, cudaMemcpyDeviceToDevice, c->st);
+}
+template <>
+void from_T<float>(pint_ctx* c, const cpx<float>* src, double* dst, size_t n) {
+  launch_copy_f2d(reinterpret_cast<const float*>(src), dst, (long long)(2 * n), c->st);
+}
+
+template <class T>
+pint_status dft_fwd_T(pint_ctx* c, Engine<T>& e, const double* x, double* xhat) {
+  const size_t n = (size_t)c->K * c->s.nblk;
+  cudaMemcpyAsync(c->ot, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->st);
+  launch_mask_blocks(c->s, c->K, 1, c->ot, c->st);
+  launch_dft_forward<T>(c->K, c->J, c->s.nblk, c->ot, e.R, e.cosk, e.sink, c->st);
+  from_T<T>(c, e.R, xhat, (size_t)c->J * c->s.nblk);
+  return c->launched("dft forward") ? PINT_OK : PINT_ERR_CUDA;
+}
+
+template <class T>
+pint_status dft_inv_T(pint_ctx* c, Engine<T>& e, const double* xhat, double* x) {
+  const size_t fl = (size_t)c->J * c->s.nblk;
+  to_T<T>(c, xhat, e.R, fl);
+  launch_dft_inverse<T>(c->K, c->J, c->s.nblk, e.R, x, e.cosk, e.sink, c->st);
+  launch_mask_blocks(c->s, c->K, 1, x, c->st);
+  return c->launched("dft inverse") ? PINT_OK : PINT_ERR_CUDA;
+}
+
+template <class T>
+pint_status freq_in(pint_ctx* c, Engine<T>& e, const double* in) {
+  // copy, zero the non-unknown entries in FP64, then convert to T
+  const size_t fl = (size_t)c->J * c->s.nblk;
+  cudaMemcpyAsync(c->ofreq, in, sizeof(double) * 2 * fl, cudaMemcpyDeviceToDevice, c->st);
+  launch_mask_blocks(c->s, c->J, 2, c->ofreq, c->st);
+  to_T<T>(c, c->ofreq, e.R, fl);
+  return PINT_OK;
+}
+
+template <class T>
+pint_status block_mv_T(pint_ctx* c, Engine<T>& e, const double* in, double* out) {
+  const size_t fl = (size_t)c->J * c->s.nblk;
+  freq_in<T>(c, e, in);
+  e.block_matvec(c->d_blkG, e.R, e.Y, nullptr);
+  from_T<T>(c, e.Y, out, fl);
+  return c->launched("block matvec") ? PINT_OK : PINT_ERR_CUDA;
+}
+
+template <class T>
+pint_status block_solve_T(pint_ctx* c, Engine<T>& e, const double* in, double* out, int* its) {
+  const size_t fl = (size_t)c->J * c->s.nblk;
+  freq_in<T>(c, e, in);
+  e.freq_solve(e.R, e.Y, its);
+  from_T<T>(c, e.Y, out, fl);
+  return c->launched("block solve") && c->cu(cudaStreamSynchronize(c->st), "block solve") ? PINT_OK
+                                                                                          : PINT_ERR_CUDA;
+}
+
+template <class T>
+pint_status component_T(pint_ctx* c, Engine<T>& e, int which, int j, const double* in, double* out) {
+  const Slots& s = c->s;
+  const int J = c->J;
+  if (which == 6) {
+    const size_t nb = (size_t)s.nblk;
+    cudaMemsetAsync(e.R, 0, sizeof(cpx<T>) * J * nb, c->st);
+    to_T<T>(c, in, e.R + (size_t)j * nb, nb);
+    std::vector<int> act(J, 0);
+    act[j] = 1;
+    cudaMemcpyAsync(c->d_active_one, act.data(), sizeof(int) * J, cudaMemcpyHostToDevice, c->st);
+    e.block_prec(e.R, e.Y, c->d_active_one);
+    from_T<T>(c, e.Y + (size_t)j * nb, out, nb);
+    return c->launched("component") && c->cu(cudaStreamSynchronize(c->st), "component") ? PINT_OK
+                                                                                         : PINT_ERR_CUDA;
+  }
+  const int space = (which == 3 || which == 5) ? 1 : 2;
+  const size_t len = space == 2 ? (size_t)s.ns : (size_t)s.nq;
+  int op;
+  switch (which) {
+    case 0:
+      if (c->oseen) return c->fail(PINT_ERR_ARG, "W_j exists for Stokes problems only");
+      op = j;
+      break;
+    case 1:
+    case 2:
+      if (!c->oseen) return c->fail(PINT_ERR_ARG, "Q_j exists for Oseen problems only");
+      op = which == 1 ? j : J + j;
+      break;
+    case 3:
+      op = 2 * J;
+      break;
+    case 4:
+      op = 2 * J + 1;
+      break;
+    default:
+      op = 2 * J + 2;
+      break;
+  }
+  // mask the input field on the host (diagnostic path)
+  std::vector<double> hin(2 * len);
+  if (!c->cu(cudaMemcpy(hin.data(), in, sizeof(double) * 2 * len, cudaMemcpyDeviceToHost), "component input"))
+    return PINT_ERR_CUDA;
+  const int n = space == 2 ? s.n2 : s.n1;
+  for (size_t q = 0; q < len; ++q) {
+    const int ix = (int)(q % n), iy = (int)(q / n);
+    const bool unk = space == 2 ? (ix > 0 && iy > 0 && ix < n - 1 && iy < n - 1) : ((ix | iy) != 0);
+    if (!unk) hin[2 * q] = hin[2 * q + 1] = 0.0;
+  }
+  double* stage = c->ot;  // FP64 scratch of kkt_len >= 2 * len doubles
+  cudaMemcpyAsync(stage, hin.data(), sizeof(double) * 2 * len, cudaMemcpyHostToDevice, c->st);
+  to_T<T>(c, stage, e.T1, len);
+  FieldJob jb{0, 0, op, 0};
+  cudaMemcpyAsync(c->j_one, &jb, sizeof(FieldJob), cudaMemcpyHostToDevice, c->st);
+  if (which <= 3)
+    e.mg(space, which == 1 || which == 2 ? c->conv : false, c->j_one, 1, e.T2, e.T1, nullptr);
+  else
+    e.cheb(space, c->j_one, 1, e.T2, e.T1, nullptr);
+  from_T<T>(c, e.T2, out, len);
+  return c->launched("component") && c->cu(cudaStreamSynchronize(c->st), "component") ? PINT_OK : PINT_ERR_CUDA;
+}
+}  // namespace
+
+extern "C" {
+
+pint_status pint_dft_forward(pint_handle h, const double* x, double* xhat) {
+  if (!h || !x || !xhat) return g_err = "null argument", PINT_ERR_ARG;
+  return h->fp32 ? dft_fwd_T<float>(h, h->e32, x, xhat) : dft_fwd_T<double>(h, h->e64, x, xhat);
+}
+
+pint_status pint_dft_inverse(pint_handle h, const double* xhat, double* x) {
+  if (!h || !x || !xhat) return g_err = "null argument", PINT_ERR_ARG;
+  return h->fp32 ? dft_inv_T<float>(h, h->e32, xhat, x) : dft_inv_T<double>(h, h->e64, xhat, x);
+}
+
+pint_status pint_freq_block_matvec(pint_handle h, const double* xhat, double* yhat) {
+  if (!h || !xhat || !yhat) return g_err = "null argument", PINT_ERR_ARG;
+  return h->fp32 ? block_mv_T<float>(h, h->e32, xhat, yhat) : block_mv_T<double>(h, h->e64, xhat, yhat);
+}
+
+pint_status pint_freq_block_solve(pint_handle h, const double* rhat, double* yhat, int* its) {
+  if (!h || !rhat || !yhat) return g_err = "null argument", PINT_ERR_ARG;
+  return h->fp32 ? block_solve_T<float>(h, h->e32, rhat, yhat, its)
+                 : block_solve_T<double>(h, h->e64, rhat, yhat, its);
+}
+
+pint_status pint_component_apply(pint_handle h, int which, int j, const double* in, double* out) {
+  if (!h || !in || !out) return g_err = "null argument", PINT_ERR_ARG;
+  if (which < 0 || which > 6) return h->fail(PINT_ERR_ARG, "which must be in [0, 6]");
+  if (j < 0 || j >= h->J) return h->fail(PINT_ERR_ARG, "frequency index out of range");
+  return h->fp32 ? component_T<float>(h, h->e32, which, j, in, out)
+                 : component_T<double>(h, h->e64, which, j, in, out);
+}
+
+const char* pint_last_error(pint_handle h) {
+  if (h && !h->err.empty()) return h->err.c_str();
+  return g_err.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,53 @@
+"""CPU checks of the C ABI: the library builds, loads and exports every
+function include/pint.h declares; argument validation needs no GPU."""
+import ctypes
+import os
+
+import pytest
+
+from paper_2405_18964_gb300 import binding
+
+
+def test_header_declares_the_boundary():
+    names = binding.header_functions()
+    for required in ["pint_create", "pint_set_data", "pint_apply_preconditioner", "pint_solve", "pint_destroy",
+                     "pint_kkt_matvec", "pint_last_error"]:
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol():
+    if not os.path.exists(binding.LIB_PATH):
+        pytest.skip("libpint.so not built (run __graft_entry__.build())")
+    L = binding.lib()
+    missing = [n for n in binding.header_functions() if not hasattr(L, n)]
+    assert missing == []
+    # every declared function has a ctypes signature in the binding
+    assert set(binding.header_functions()) == set(binding._SIGS)
+
+
+def test_struct_layouts_match_header_field_order():
+    src = open(binding.HEADER).read()
+    body = src[src.index("typedef struct {\n  int kind;"):src.index("} pint_params;")]
+    order = []
+    for line in body.splitlines():
+        line = line.split("/*")[0].strip().rstrip(";")
+        if not line or line.startswith("typedef"):
+            continue
+        typ, names = line.split(None, 1)
+        order += [n.strip() for n in names.split(",")]
+    assert order == [f[0] for f in binding.Params._fields_]
+
+
+def test_default_params_and_argument_validation():
+    if not os.path.exists(binding.LIB_PATH):
+        pytest.skip("libpint.so not built")
+    p = binding.default_params()
+    assert (p.mg_cycles, p.cheb_steps, p.uzawa_steps, p.uzawa_mu, p.inner_tol) == (4, 10, 6, 0.75, 1e-2)
+    h = ctypes.c_void_p()
+    bad = binding.default_params(level=0)
+    assert binding.lib().pint_create(ctypes.byref(bad), None, ctypes.byref(h)) == 1
+    assert b"level" in binding.lib().pint_last_error(None)
+    bad = binding.default_params(kind=1, wind=1, x0=0.0, x1=1.0)
+    assert binding.lib().pint_create(ctypes.byref(bad), None, ctypes.byref(h)) == 1
+    assert b"[-1,1]" in binding.lib().pint_last_error(None)
+    assert binding.lib().pint_destroy(None) == 0
