@@ -1,0 +1,385 @@
+#!/usr/bin/env python
+"""Benchmark: KKT solves/s to relative residual 1e-8 for the unsteady Stokes
+control problem (Q2-Q1, 64x64 elements, n_t = 256 time blocks on T = 1,
+beta in {1e-2, 1e-4, 1e-6}, seeded divergence-free desired state), with the
+FP32 parallel-in-time preconditioner inside FP64 FGMRES(30); the plain FP64
+preconditioner is timed beside it.
+
+One step = one complete solve (right-hand side resident, x0 = 0): outer
+FGMRES, KKT matvecs, and in every preconditioner apply the time DFT, the
+Stokes transforms, the batched inner GMRES with multigrid / Chebyshev
+commutator preconditioning over all frequencies, and the inverse DFT.
+Steps cycle through the three beta values.  Inputs are larger than L2 (the
+FP64 FGMRES basis alone is 9.4 GB), so no flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Multi-GPU: replicas only (each rank solves its own problems; no collective
+on the data path), launched by torch.distributed.run.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    # configs: Stokes control, 64x64 Q2-Q1 grid, n_t = 256, T = 1
+    "stokes64_nt256": dict(kind=0, level=6, K=256, T=1.0, betas=[1e-2, 1e-4, 1e-6], nu=1e-2, x0=0.0, x1=1.0,
+                           wind=0),
+    # same grid with n_t = 32: a shorter run of the same kernels, for profiling
+    "stokes64_nt32": dict(kind=0, level=6, K=32, T=1.0, betas=[1e-4], nu=1e-2, x0=0.0, x1=1.0, wind=0),
+    # small case the oracle solves in seconds (8x8 grid, n_t = 8)
+    "stokes8_nt8": dict(kind=0, level=3, K=8, T=1.0, betas=[1e-2], nu=1e-2, x0=0.0, x1=1.0, wind=0),
+}
+# FGMRES iterations per solve measured on the GB300 (FP64 and FP32 preconditioner
+# agree) for the middle beta of each workload; used to extrapolate the oracle's
+# per-block time to a whole solve in the reference arm.
+OUTER_ITS_MEASURED = {"stokes64_nt256": 21, "stokes64_nt32": 21, "stokes8_nt8": 14}
+METRIC = "KKT solves/s to rel-res 1e-8 (FP32 precond vs FP64 plain); p50/p99 latency"
+UNIT = "solves/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="stokes64_nt256", choices=list(WORKLOADS))
+    ap.add_argument("--fp64-budget-s", type=float, default=20.0,
+                    help="wall-clock budget for the FP64-plain comparison solves")
+    ap.add_argument("--cpu-sample-s", type=float, default=20.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------- helpers
+class Clocks:
+    """nvidia-smi sampler run during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+def dist_init():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws <= 1:
+        return 0, 1, None
+    import torch.distributed as dist
+    rank = int(os.environ["RANK"])
+    local = int(os.environ.get("LOCAL_RANK", rank))
+    import torch
+    torch.cuda.set_device(local)
+    dist.init_process_group("nccl", init_method="env://")
+    return rank, ws, dist
+
+
+def algorithmic_bytes_mg_q2(sizes, nlaunch_jobs, cycles, bw):
+    """Per-unit figure for one V-cycle on one complex Q2 field with 2+2
+    sweeps: 24 n c b_w bytes (n nodes, c = 2, b_w bytes per word)."""
+    return 24.0 * sizes.n_s * 2 * bw * cycles * nlaunch_jobs
+
+
+# ------------------------------------------------------------- our arm
+def run_ours(a):
+    import torch
+    from paper_2405_18964_gb300 import binding, inputs
+
+    rank, ws, dist = dist_init()
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    W = WORKLOADS[a.workload]
+    K, T = W["K"], W["T"]
+    tau = T / (K + 1)
+    stream = torch.cuda.current_stream()
+    N = 2 ** W["level"]
+
+    def make(beta, prec, seed):
+        p = binding.default_params(kind=W["kind"], level=W["level"], n_t=K, tau=tau, beta=beta, nu=W["nu"],
+                                   x0=W["x0"], x1=W["x1"], wind=W["wind"], prec=prec)
+        G = binding.Problem(p, stream=stream.cuda_stream)
+        vd = inputs.desired_state(N, W["x0"], W["x1"], K, tau, T, seed)
+        G.set_data(vd)
+        return G, vd
+
+    probs = [make(b, 1, 1000 * rank + i) for i, b in enumerate(W["betas"])]
+    n = probs[0][0].kkt_len
+    x = torch.zeros(n, dtype=torch.float64, device="cuda")
+
+    def step(i, prof=None):
+        G = probs[i % len(probs)][0]
+        x.zero_()
+        return G.solve(x)
+
+    for i in range(a.warmup):
+        step(i)
+    torch.cuda.synchronize()
+    # ---- timed region (device-resident inputs)
+    for G, _ in probs:
+        G.profile_enable(["mg_q2"])
+    clk = Clocks(dev)
+    clk.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps + 1)]
+    ev[0].record(stream)
+    infos = []
+    for i in range(a.steps):
+        infos.append(step(i))
+        ev[i + 1].record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = clk.stop()
+    lat = [ev[i].elapsed_time(ev[i + 1]) for i in range(a.steps)]
+    total_ms = ev[0].elapsed_time(ev[-1])
+    if dist:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    prof = [G.profile_read() for G, _ in probs]
+    mg = {k: sum(p["mg_q2"][k] for p in prof) for k in ("launches", "timed", "ms")}
+    launches = sum(sum(c["launches"] for c in p.values()) for p in prof)
+    value = a.steps * ws / (total_ms / 1e3)
+
+    # ---- per-class shares from one fully profiled solve (outside the timed region)
+    G0 = probs[0][0]
+    G0.profile_enable(binding.PROF_CLASSES)
+    step(0)
+    share = G0.profile_read()
+    tot = sum(c["ms"] for c in share.values()) or 1.0
+    shares = {k: round(c["ms"] / tot, 4) for k, c in share.items() if c["launches"]}
+    G0.profile_enable([])
+
+    # ---- e2e through the public API with host buffers (pinned)
+    vd_pinned = [torch.from_numpy(vd).pin_memory() for _, vd in probs]
+    xh = torch.zeros(n, dtype=torch.float64).pin_memory()
+    xnp = xh.numpy()
+    e2e_ms = []
+    for i in range(a.steps):
+        G = probs[i % len(probs)][0]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        G.set_data(vd_pinned[i % len(probs)].numpy())
+        xnp[:] = 0.0
+        G.solve_host(xnp)
+        torch.cuda.synchronize()
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    h2d = int(vd_pinned[0].numel() * 8 + n * 8)
+    d2h = int(n * 8)
+    e2e = {"value": a.steps * ws / (sum(e2e_ms) / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+           "d2h_bytes_per_step": d2h}
+
+    # ---- FP64 plain preconditioner, same problems, within a time budget
+    fp64 = {"solves": 0, "ms": 0.0}
+    t_start = time.perf_counter()
+    errs, its64 = [], []
+    x64 = torch.zeros(n, dtype=torch.float64, device="cuda")
+    for i, b in enumerate(W["betas"]):
+        if a.fp64_budget_s <= 0 or time.perf_counter() - t_start > a.fp64_budget_s:
+            break
+        G64, _ = make(b, 0, 1000 * rank + i)
+        x64.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        inf = G64.solve(x64)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        fp64["solves"] += 1
+        fp64["ms"] += e0.elapsed_time(e1)
+        its64.append(inf.outer_iterations)
+        x.zero_()
+        probs[i][0].solve(x)
+        errs.append(float(torch.linalg.norm(x - x64) / torch.linalg.norm(x64)))
+        G64.close()
+    fp64_value = fp64["solves"] / (fp64["ms"] / 1e3) if fp64["solves"] else None
+
+    # ---- roofline of the dominant kernel (multigrid on the velocity fields)
+    hbm, src = peaks()
+    J = probs[0][0].sizes.J
+    per_launch_jobs = 4 * J
+    alg = algorithmic_bytes_mg_q2(probs[0][0].sizes, per_launch_jobs, 4, 4)
+    avg_ms = mg["ms"] / max(1, mg["timed"])
+    achieved = alg / (avg_ms / 1e3) / 1e9 if mg["timed"] else None
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "mg_q2_traffic.json")
+    if os.path.exists(tpath):
+        traffic = json.load(open(tpath)).get("bytes_per_launch")
+
+    line = {
+        "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": ws, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": round(total_ms / a.steps, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 preconditioner / f64 FGMRES",
+        "data": "synthetic (seeded curl of 4 random sine modes)",
+        "config": {"workload": a.workload, "kind": "stokes", "grid": f"{N}x{N} Q2-Q1", "n_t": K, "T": T,
+                   "betas": W["betas"], "nu": W["nu"], "outer": "FGMRES(30), tol 1e-8", "inner_tol": 1e-2,
+                   "l2": "inputs larger than L2 (FP64 FGMRES basis 9.4 GB)", "parallelism": f"replicas x{ws}"},
+        "latency_ms": {"p50": round(float(np.percentile(lat, 50)), 3), "p99": round(float(np.percentile(lat, 99)), 3)},
+        "outer_iterations": [inf.outer_iterations for inf in infos],
+        "relres": [inf.relres for inf in infos],
+        "fp64_plain": {"value": round(fp64_value, 5) if fp64_value else None, "unit": UNIT,
+                       "solves": fp64["solves"], "outer_iterations": its64,
+                       "speedup_fp32_over_fp64": round(value / fp64_value, 2) if fp64_value else None,
+                       "fp32_vs_fp64_solution_relerr": errs},
+        "e2e": e2e,
+        "gpu_launches": int(launches),
+        "kernel_time_share": shares,
+        "roofline": {"kernel": "mg_kernel<float,Q2> (multigrid W_j, 4 V-cycles, all frequencies x 4 fields)",
+                     "bound": "hbm", "achieved": round(achieved, 1) if achieved else None,
+                     "peak": hbm, "peak_source": src, "unit": "GB/s",
+                     "frac": round(achieved / hbm, 4) if achieved else None, "traffic": traffic,
+                     "avg_launch_ms": round(avg_ms, 4), "timed_launches": mg["timed"],
+                     "algorithmic_bytes_per_launch": alg},
+        "clocks": clocks,
+    }
+    if rank == 0 and not a.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(W, a.cpu_sample_s, its64 or [inf.outer_iterations for inf in infos])
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    for G, _ in probs:
+        G.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+# --------------------------------------------------------- oracle timing
+def cpu_baseline(W, budget_s, outer_its):
+    """The FP64 oracle's nested solver (Algorithm 2 with the same multigrid,
+    Chebyshev and inner GMRES definitions) timed on the host cores on a
+    bounded sample: whole frequency-block solves at the full grid size,
+    extrapolated to K blocks per preconditioner apply and the measured
+    outer iteration count per solve."""
+    from oracle import inexact, kkt
+    from paper_2405_18964_gb300 import inputs
+    K, T = W["K"], W["T"]
+    tau = T / (K + 1)
+    beta = W["betas"][len(W["betas"]) // 2]
+    P = kkt.Problem("stokes", W["level"], K, tau, beta, W["nu"], W["x0"], W["x1"], None)
+    pc = inexact.PinTPreconditioner(P)
+    rng = np.random.default_rng(0)
+    t0 = time.perf_counter()
+    done, js = 0, []
+    while True:
+        j = 1 + done % max(1, K // 2)
+        g = rng.standard_normal(2 * P.nb) + 1j * rng.standard_normal(2 * P.nb)
+        pc.solve_block(j, g)
+        js.append(j)
+        done += 1
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    per_block = (time.perf_counter() - t0) / done
+    its = float(np.mean(outer_its)) if outer_its else 1.0
+    est_solve_s = its * K * per_block
+    cores = len(os.sched_getaffinity(0))
+    return {"value": round(1.0 / est_solve_s, 8), "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{done} frequency-block solves (Algorithm 2, j in {sorted(set(js))}, beta={beta}) at "
+                      f"{2**W['level']}x{2**W['level']}; {per_block:.2f} s/block x {K} blocks/apply x "
+                      f"{its:.1f} outer its (extrapolated)",
+            "threads": os.environ.get("OMP_NUM_THREADS", "default")}
+
+
+def run_reference(a):
+    """The oracle as it stands, on the host cores, same metric and workload;
+    each step a bounded sample (one frequency-block solve), extrapolated."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle import inexact, kkt
+    W = WORKLOADS[a.workload]
+    K, T = W["K"], W["T"]
+    tau = T / (K + 1)
+    beta = W["betas"][len(W["betas"]) // 2]
+    P = kkt.Problem("stokes", W["level"], K, tau, beta, W["nu"], W["x0"], W["x1"], None)
+    pc = inexact.PinTPreconditioner(P)
+    rng = np.random.default_rng(0)
+    g = rng.standard_normal(2 * P.nb) + 1j * rng.standard_normal(2 * P.nb)
+    for i in range(a.warmup):
+        pc.solve_block(1 + i % (K // 2), g)
+    t0 = time.perf_counter()
+    per = []
+    for i in range(a.steps):
+        s0 = time.perf_counter()
+        pc.solve_block(1 + i % (K // 2), g)
+        per.append(time.perf_counter() - s0)
+    dt = time.perf_counter() - t0
+    outer_its = OUTER_ITS_MEASURED[a.workload]
+    est = outer_its * K * (dt / a.steps)
+    cores = len(os.sched_getaffinity(0))
+    v = 1.0 / est
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": round(v, 8), "unit": UNIT, "n_gpus": a.gpus,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": round(dt / a.steps * 1e3, 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": a.workload, "beta": beta},
+        "cpu_baseline": {"kind": "oracle", "cores": cores, "value": round(v, 8), "unit": UNIT,
+                         "sample": f"one frequency-block solve per step ({dt / a.steps:.2f} s), x {K} blocks x "
+                                   f"{outer_its} outer its (extrapolated)"},
+        "e2e": {"value": round(v, 8), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+        return
+    from paper_2405_18964_gb300 import binding
+    if not os.path.exists(binding.LIB_PATH):
+        import __graft_entry__
+        __graft_entry__.build()
+    run_ours(a)
+
+
+if __name__ == "__main__":
+    main()

@@ -195,6 +195,36 @@ pint_status pint_freq_block_solve(pint_handle h, const double* rhat_dev, double*
 pint_status pint_component_apply(pint_handle h, int which, int j, const double* in_dev,
                                  double* out_dev);
 
+/* ---- tracing ------------------------------------------------------------
+ * Kernel classes of the hot path.  Launch counts are always kept; CUDA-event
+ * timing (events recorded on the handle's stream around each launch of a
+ * class) is kept for the classes whose bit is set in the mask. */
+enum {
+  PINT_PROF_MG_Q2 = 0,      /* multigrid on velocity fields (W_j, Q_j, Q_j^H)  */
+  PINT_PROF_MG_Q1 = 1,      /* multigrid on pressure fields (K_p)              */
+  PINT_PROF_CHEB = 2,       /* Chebyshev semi-iteration (M, M_p)               */
+  PINT_PROF_DFT_FWD = 3,    /* forward time DFT                                */
+  PINT_PROF_DFT_INV = 4,    /* inverse time DFT                                */
+  PINT_PROF_BLOCK_MV = 5,   /* frequency-block matvec (G_j / Z_j)              */
+  PINT_PROF_COMBO = 6,      /* operator combinations, transforms, axpys        */
+  PINT_PROF_INNER = 7,      /* inner GMRES reductions, Givens, updates         */
+  PINT_PROF_KKT_MV = 8,     /* FP64 KKT matvec (Eq. FinalA)                    */
+  PINT_PROF_OUTER = 9,      /* outer FGMRES vector kernels                     */
+  PINT_PROF_OTHER = 10,     /* masking, conversions, right-hand side           */
+  PINT_PROF_CLASSES = 11
+};
+
+typedef struct {
+  long long launches[PINT_PROF_CLASSES]; /* kernels launched since the reset    */
+  long long timed[PINT_PROF_CLASSES];    /* launches covered by event timing    */
+  double ms[PINT_PROF_CLASSES];          /* summed event time of timed launches */
+} pint_profile;
+
+/* Reset the counters and select the timed classes (bit i = class i). */
+pint_status pint_profile_enable(pint_handle h, unsigned mask);
+/* Synchronise the handle's stream and copy the counters out. */
+pint_status pint_profile_read(pint_handle h, pint_profile* out);
+
 const char* pint_last_error(pint_handle h);
 
 #ifdef __cplusplus

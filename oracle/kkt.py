@@ -167,21 +167,34 @@ class Problem:
     def pc_inverse(self, r, block_solver=None):
         """P_C^{-1} r by diagonalisation (Sec. 3.1):  r^ = F r along time,
         one block solve per frequency, then F^{-1}.  `block_solver(j, rhs)`
-        defaults to a sparse LU solve with G_bar(j); all K frequencies are
-        solved (no Hermitian shortcut), and the real part is returned."""
+        defaults to a sparse LU solve with G_bar(j) (factorisations cached);
+        all K frequencies are solved (no Hermitian shortcut), and the real
+        part is returned."""
+
         K, nb = self.K, self.nb
         R = r.reshape(2, K, nb)
         Rh = np.fft.fft(R, axis=1)                     # F along time, per group
         Yh = np.empty_like(Rh)
+        if block_solver is None and not hasattr(self, "_lu"):
+            self._lu = {}
         for j in range(K):
             rhs = np.concatenate([Rh[0, j], Rh[1, j]])
             if block_solver is None:
-                sol = spla.splu(self.G_bar(j)).solve(rhs)
+                if j not in self._lu:
+                    self._lu[j] = spla.splu(self.G_bar(j))
+                sol = self._lu[j].solve(rhs)
             else:
                 sol = block_solver(j, rhs)
             Yh[0, j], Yh[1, j] = sol[:nb], sol[nb:]
         Y = np.fft.ifft(Yh, axis=1)
         return Y.real.ravel(), Y
+
+    def reference_solution(self, b, tol=1e-12):
+        """Reference solution of A x = b: FP64 FGMRES preconditioned by the
+        exact P_C^{-1} (Theorem 1 bounds its iterations by 2 n_v + 1)."""
+        x, info = fgmres(self.kkt_matrix(), b, lambda v: self.pc_inverse(v)[0], tol=tol,
+                         restart=min(200, 2 * self.nv + 2), maxit=4 * self.nv + 10)
+        return x, info
 
 
 def fgmres(A, b, Pinv, x0=None, restart=30, tol=1e-8, maxit=1000):

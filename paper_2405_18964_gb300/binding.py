@@ -50,6 +50,15 @@ class Sizes(ctypes.Structure):
                 ("freq_len", ctypes.c_size_t), ("device_bytes", ctypes.c_size_t)]
 
 
+PROF_CLASSES = ["mg_q2", "mg_q1", "cheb", "dft_fwd", "dft_inv", "block_mv", "combo", "inner", "kkt_mv", "outer",
+                "other"]
+
+
+class Profile(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_longlong * 11), ("timed", ctypes.c_longlong * 11),
+                ("ms", ctypes.c_double * 11)]
+
+
 _lib = None
 _P = ctypes.c_void_p
 _SIGS = {
@@ -68,6 +77,8 @@ _SIGS = {
     "pint_freq_block_matvec": (ctypes.c_int, [_P, _P, _P]),
     "pint_freq_block_solve": (ctypes.c_int, [_P, _P, _P, _P]),
     "pint_component_apply": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P, _P]),
+    "pint_profile_enable": (ctypes.c_int, [_P, ctypes.c_uint]),
+    "pint_profile_read": (ctypes.c_int, [_P, ctypes.POINTER(Profile)]),
     "pint_last_error": (ctypes.c_char_p, [_P]),
 }
 
@@ -225,6 +236,19 @@ class Problem:
         _check(lib().pint_freq_block_solve(self.h, _dptr(rhat, "complex128", self.freq_len),
                                            _dptr(yhat, "complex128", self.freq_len), its), self.h)
         return list(its)
+
+    def profile_enable(self, classes=()):
+        """Reset the counters; time the named kernel classes with CUDA events."""
+        mask = 0
+        for c in classes:
+            mask |= 1 << PROF_CLASSES.index(c)
+        _check(lib().pint_profile_enable(self.h, mask), self.h)
+
+    def profile_read(self):
+        p = Profile()
+        _check(lib().pint_profile_read(self.h, ctypes.byref(p)), self.h)
+        return {c: {"launches": p.launches[i], "timed": p.timed[i], "ms": p.ms[i]}
+                for i, c in enumerate(PROF_CLASSES)}
 
     def component_apply(self, which, j, x, y):
         w = COMPONENT[which] if isinstance(which, str) else int(which)

@@ -111,6 +111,43 @@ struct pint_ctx {
   Engine<double> e64;
   Engine<float> e32;
 
+  // ---- tracing: launch counts per kernel class, event timing for masked classes
+  unsigned prof_mask = 0;
+  long long prof_launch[PINT_PROF_CLASSES] = {};
+  long long prof_timed[PINT_PROF_CLASSES] = {};
+  double prof_ms[PINT_PROF_CLASSES] = {};
+  struct Pend {
+    int cls;
+    cudaEvent_t a, b;
+  };
+  std::vector<Pend> pend;
+  std::vector<cudaEvent_t> evpool;
+  cudaEvent_t take_event() {
+    if (!evpool.empty()) {
+      cudaEvent_t e = evpool.back();
+      evpool.pop_back();
+      return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+  }
+  // Fold completed event pairs into the counters (call after a stream sync).
+  void drain() {
+    for (auto& q : pend) {
+      float t = 0.f;
+      if (cudaEventElapsedTime(&t, q.a, q.b) == cudaSuccess) {
+        prof_ms[q.cls] += t;
+        prof_timed[q.cls]++;
+      } else {
+        cudaGetLastError();
+      }
+      evpool.push_back(q.a);
+      evpool.push_back(q.b);
+    }
+    pend.clear();
+  }
+
   // ----------------------------------------------------------- helpers
   pint_status fail(pint_status code, const std::string& m) {
     err = m;
@@ -143,6 +180,34 @@ struct pint_ctx {
   }
   bool launched(const char* what) { return cu(cudaGetLastError(), what); }
 };
+
+// RAII scope around the launches of one kernel class: counts nk kernels and,
+// if the class is being timed, records a CUDA event pair on the stream.
+struct Prof {
+  pint_ctx* c;
+  int cls;
+  cudaEvent_t a = nullptr;
+  Prof(pint_ctx* c_, int cls_, int nk) : c(c_), cls(cls_) {
+    c->prof_launch[cls] += nk;
+    if ((c->prof_mask >> cls) & 1u) {
+      a = c->take_event();
+      cudaEventRecord(a, c->st);
+    }
+  }
+  ~Prof() {
+    if (!a) return;
+    cudaEvent_t b = c->take_event();
+    cudaEventRecord(b, c->st);
+    c->pend.push_back({cls, a, b});
+    if (c->pend.size() > 8192) {
+      cudaStreamSynchronize(c->st);
+      c->drain();
+    }
+  }
+};
+#define PROF_CAT2(a, b) a##b
+#define PROF_CAT(a, b) PROF_CAT2(a, b)
+#define PROF(ctx, cls, nk) Prof PROF_CAT(prof_scope_, __LINE__)((ctx), (cls), (nk))
 
 // ============================================================================
 // Engine<T>
@@ -178,6 +243,7 @@ void Engine<T>::mg(int space, bool conv, const FieldJob* jobs, int njobs, cpx<T>
   L.omega = c->p.sor_omega;
   L.space = space;
   L.conv = conv;
+  PROF(c, space == 2 ? PINT_PROF_MG_Q2 : PINT_PROF_MG_Q1, 1);
   launch_mg<T>(L, c->st);
 }
 
@@ -196,6 +262,7 @@ void Engine<T>::cheb(int space, const FieldJob* jobs, int njobs, cpx<T>* xb, con
   L.lmin = space == 2 ? Q2_LMIN : Q1_LMIN;
   L.lmax = space == 2 ? Q2_LMAX : Q1_LMAX;
   L.space = space;
+  PROF(c, PINT_PROF_CHEB, 1);
   launch_cheb<T>(L, c->st);
 }
 
@@ -211,6 +278,7 @@ void Engine<T>::block_matvec(const BlkCoef* coef, const cpx<T>* X, cpx<T>* Out, 
   a.active = active;
   a.x = X;
   a.y = Out;
+  PROF(c, PINT_PROF_BLOCK_MV, 2);
   launch_block_matvec<T>(a, c->st);
 }
 
@@ -227,8 +295,8 @@ void Engine<T>::block_prec(const cpx<T>* U, cpx<T>* Out, const int* active) {
     // S^_j^{-1} = (1 + c1) K_p^{-1} + nu c2 M_p^{-1} on the p and mu blocks
     mg(1, false, c->j_Kp2, 2 * J, T1, U, active);
     cheb(1, c->j_Mp2, 2 * J, T2, U, active);
-    launch_lincomb<T>(J, s.nblk, s.nq, Out, s.p, T1, s.p, c->d_sa, T2, s.p, c->d_sb, active, st);
-    launch_lincomb<T>(J, s.nblk, s.nq, Out, s.mu, T1, s.mu, c->d_sa, T2, s.mu, c->d_sb, active, st);
+    { PROF(c, PINT_PROF_COMBO, 1); launch_lincomb<T>(J, s.nblk, s.nq, Out, s.p, T1, s.p, c->d_sa, T2, s.p, c->d_sb, active, st); }
+    { PROF(c, PINT_PROF_COMBO, 1); launch_lincomb<T>(J, s.nblk, s.nq, Out, s.mu, T1, s.mu, c->d_sa, T2, s.mu, c->d_sb, active, st); }
     return;
   }
   // ---- Oseen: Uzawa (Eq. Uzawa11) on G^(1,1), x^(0) = 0
@@ -251,10 +319,10 @@ void Engine<T>::block_prec(const cpx<T>* U, cpx<T>* Out, const int* active) {
     ca.x = Out;
     ca.z = U;
     ca.out = T1;
-    launch_combo<T>(ca, st);
+    { PROF(c, PINT_PROF_COMBO, 1); launch_combo<T>(ca, st); }
     // x1 += (1/tau) M^-1 T1[v]   (M^ = Chebyshev)
     cheb(2, c->j_M2, 2 * J, T2, T1, active);
-    launch_lincomb<T>(J, s.nblk, lenv, Out, s.vx, Out, s.vx, c->d_one, T2, s.vx, c->d_invtau, active, st);
+    { PROF(c, PINT_PROF_COMBO, 1); launch_lincomb<T>(J, s.nblk, lenv, Out, s.vx, Out, s.vx, c->d_one, T2, s.vx, c->d_invtau, active, st); }
     // T1[lam] = b2 - (d M + tau L) x1 + tau/beta M x2
     ca.coef = c->d_cuzd;
     ca.rows[0] = ComboRow{s.lx, s.lx, {s.vx, s.lx}, 0, {1, 2}, 2, 1};
@@ -262,7 +330,7 @@ void Engine<T>::block_prec(const cpx<T>* U, cpx<T>* Out, const int* active) {
     ca.x = Out;
     ca.z = U;
     ca.out = T1;
-    launch_combo<T>(ca, st);
+    { PROF(c, PINT_PROF_COMBO, 1); launch_combo<T>(ca, st); }
     // S^^{-1} = tau Q^{-H} M Q^{-1}
     mg(2, c->conv, c->j_Q2, 2 * J, T2, T1, active);
     ca.coef = c->d_cmass;
@@ -272,10 +340,10 @@ void Engine<T>::block_prec(const cpx<T>* U, cpx<T>* Out, const int* active) {
     ca.x = T2;
     ca.z = nullptr;
     ca.out = T3;
-    launch_combo<T>(ca, st);
+    { PROF(c, PINT_PROF_COMBO, 1); launch_combo<T>(ca, st); }
     mg(2, c->conv, c->j_QH2, 2 * J, T1, T3, active);
     // x2 -= (1/mu) tau Q^{-H} M Q^{-1} (...)
-    launch_lincomb<T>(J, s.nblk, lenv, Out, s.lx, Out, s.lx, c->d_one, T1, s.lx, c->d_mtaumu, active, st);
+    { PROF(c, PINT_PROF_COMBO, 1); launch_lincomb<T>(J, s.nblk, lenv, Out, s.lx, Out, s.lx, c->d_one, T1, s.lx, c->d_mtaumu, active, st); }
   }
   // ---- Algorithm 3: y34 = -S^_j^{-1} (r34 - tau (B y2; B y1))
   BResArgs<T> br{};
@@ -293,7 +361,10 @@ void Engine<T>::block_prec(const cpx<T>* U, cpx<T>* Out, const int* active) {
   br.x = Out;
   br.z = U;
   br.out = T1;
-  launch_bres<T>(br, st);
+  {
+    PROF(c, PINT_PROF_COMBO, 1);
+    launch_bres<T>(br, st);
+  }
   // swap + (tau M_p)^{-1}: T2[p] = Cheb(T1[mu]), T2[mu] = Cheb(T1[p]) (1/tau folded below)
   cheb(1, c->j_Mp2s, 2 * J, T2, T1, active);
   // X_p, the second swap's sign and the 1/tau factors
@@ -312,7 +383,7 @@ void Engine<T>::block_prec(const cpx<T>* U, cpx<T>* Out, const int* active) {
   cq.x = T2;
   cq.z = nullptr;
   cq.out = T3;
-  launch_combo<T>(cq, st);
+  { PROF(c, PINT_PROF_COMBO, 1); launch_combo<T>(cq, st); }
   // swap + (tau K_p)^{-1}: Out[p] = MG(T3[mu]), Out[mu] = MG(T3[p])
   mg(1, false, c->j_Kp2s, 2 * J, Out, T3, active);
 }
@@ -334,15 +405,19 @@ void Engine<T>::inner_solve(const cpx<T>* S, cpx<T>* X, int* its_host) {
   const int m = G.m;
   const long long hs = (long long)(m + 1) * m * 2;  // H stride per frequency (doubles)
   const size_t vs = (size_t)J * nb;                 // one basis vector (all frequencies)
-  launch_bdot<T>(J, nb, S, S, nb, nb, G.partial, G.g, (long long)(m + 1) * 2, nullptr, false, st);
-  launch_gmres_start(G, st);
-  launch_bscale_inv<T>(J, nb, S, V, nb, G.beta0, 1, G.active, st);
+  {
+    PROF(c, PINT_PROF_INNER, 4);
+    launch_bdot<T>(J, nb, S, S, nb, nb, G.partial, G.g, (long long)(m + 1) * 2, nullptr, false, st);
+    launch_gmres_start(G, st);
+    launch_bscale_inv<T>(J, nb, S, V, nb, G.beta0, 1, G.active, st);
+  }
   for (int i = 0; i < m; ++i) {
     cpx<T>* Vi = V + (size_t)i * vs;
     cpx<T>* Zi = Z + (size_t)i * vs;
     cpx<T>* Vn = V + (size_t)(i + 1) * vs;
     block_prec(Vi, Zi, G.active);
     block_matvec(c->d_blkZ, Zi, Vn, G.active);
+    PROF(c, PINT_PROF_INNER, 3 * (i + 1) + 4);
     for (int l = 0; l <= i; ++l) {
       double* h = G.H + ((size_t)l * m + i) * 2;
       launch_bdot<T>(J, nb, V + (size_t)l * vs, Vn, nb, nb, G.partial, h, hs, G.active, false, st);
@@ -354,9 +429,13 @@ void Engine<T>::inner_solve(const cpx<T>* S, cpx<T>* X, int* its_host) {
     launch_gmres_givens(G, i, c->p.inner_tol, c->p.fixed_inner_its, st);
     cudaMemcpyAsync(c->h_count, G.count, sizeof(int), cudaMemcpyDeviceToHost, st);
     cudaStreamSynchronize(st);
+    c->drain();
     if (*c->h_count == 0) break;
   }
-  launch_gmres_finish<T>(G, nb, Z, (long long)vs, X, st);
+  {
+    PROF(c, PINT_PROF_INNER, 2);
+    launch_gmres_finish<T>(G, nb, Z, (long long)vs, X, st);
+  }
   if (its_host) {
     cudaMemcpyAsync(its_host, G.its, sizeof(int) * J, cudaMemcpyDeviceToHost, st);
     cudaStreamSynchronize(st);
@@ -366,9 +445,15 @@ void Engine<T>::inner_solve(const cpx<T>* S, cpx<T>* X, int* its_host) {
 template <class T>
 void Engine<T>::freq_solve(cpx<T>* Rin, cpx<T>* Out, int* its_host) {
   if (!c->oseen) {
-    launch_stokes_transform<T>(0, c->J, c->s, c->d_tc, Rin, c->st);
+    {
+      PROF(c, PINT_PROF_COMBO, 1);
+      launch_stokes_transform<T>(0, c->J, c->s, c->d_tc, Rin, c->st);
+    }
     inner_solve(Rin, Out, its_host);
-    launch_stokes_transform<T>(1, c->J, c->s, c->d_tc, Out, c->st);
+    {
+      PROF(c, PINT_PROF_COMBO, 1);
+      launch_stokes_transform<T>(1, c->J, c->s, c->d_tc, Out, c->st);
+    }
   } else {
     inner_solve(Rin, Out, its_host);
   }
@@ -376,8 +461,12 @@ void Engine<T>::freq_solve(cpx<T>* Rin, cpx<T>* Out, int* its_host) {
 
 template <class T>
 void Engine<T>::apply(const double* r, double* z, int* its_host) {
-  launch_dft_forward<T>(c->K, c->J, c->s.nblk, r, R, cosk, sink, c->st);
+  {
+    PROF(c, PINT_PROF_DFT_FWD, 1);
+    launch_dft_forward<T>(c->K, c->J, c->s.nblk, r, R, cosk, sink, c->st);
+  }
   freq_solve(R, Y, its_host);
+  PROF(c, PINT_PROF_DFT_INV, 1);
   launch_dft_inverse<T>(c->K, c->J, c->s.nblk, Y, z, cosk, sink, c->st);
 }
 
@@ -544,8 +633,8 @@ pint_status build(pint_ctx* c) {
       space[j] = 2;
     } else {
       // Q_j = d_j M + tau (nu K + N) + tau/sqrt(beta) M ; Q_j^H with N^T = -N
-      ops[j] = OpCoef{dr[j] + tau * sb, -dc[j], tau * nu, tau};
-      ops[J + j] = OpCoef{dr[j] + tau * sb, dc[j], tau * nu, -tau};
+      ops[j] = OpCoef{dr[j] + tau * sb, dc[j], tau * nu, tau};
+      ops[J + j] = OpCoef{dr[j] + tau * sb, -dc[j], tau * nu, -tau};
       space[j] = space[J + j] = 2;
       convf[j] = convf[J + j] = c->conv ? 1 : 0;
     }
@@ -575,7 +664,8 @@ pint_status build(pint_ctx* c) {
   // frequency-block coefficients: G_j (Eq. SubBlockG) and Z_j (Eq. GJTransformation)
   std::vector<BlkCoef> bz(J), bg(J);
   for (int j = 0; j < J; ++j) {
-    bg[j] = BlkCoef{tau, 0, dr[j], dc[j], dr[j], -dc[j], -tau / beta, 0, tau, tau, tau, 0};
+    // a12 = conj(d_j), a21 = d_j with d_j = dr + i dc
+    bg[j] = BlkCoef{tau, 0, dr[j], -dc[j], dr[j], dc[j], -tau / beta, 0, tau, tau, tau, 0};
     bz[j] = c->oseen ? bg[j] : BlkCoef{1, 0, c1[j], 0, c1[j], 0, -1, 0, c2[j], c2[j], 1, 0};
   }
   std::vector<double> tc(3 * (size_t)J), sa(2 * (size_t)J), sbv(2 * (size_t)J);
@@ -594,10 +684,10 @@ pint_status build(pint_ctx* c) {
     // T1[v] = 1 b1 + (-tau M) x1 + (-(conj d) M - tau nu K + tau N) x2
     cuza[3 * j + 0] = OpCoef{1, 0, 0, 0};
     cuza[3 * j + 1] = OpCoef{-tau, 0, 0, 0};
-    cuza[3 * j + 2] = OpCoef{-dr[j], -dc[j], -tau * nu, tau};
+    cuza[3 * j + 2] = OpCoef{-dr[j], dc[j], -tau * nu, tau};
     // T1[lam] = 1 b2 + (-d M - tau nu K - tau N) x1 + (tau/beta M) x2
     cuzd[3 * j + 0] = OpCoef{1, 0, 0, 0};
-    cuzd[3 * j + 1] = OpCoef{-dr[j], dc[j], -tau * nu, -tau};
+    cuzd[3 * j + 1] = OpCoef{-dr[j], -dc[j], -tau * nu, -tau};
     cuzd[3 * j + 2] = OpCoef{tau / beta, 0, 0, 0};
     cmass[2 * j + 0] = OpCoef{0, 0, 0, 0};
     cmass[2 * j + 1] = OpCoef{1, 0, 0, 0};
@@ -689,6 +779,8 @@ pint_status build(pint_ctx* c) {
 void free_ctx(pint_ctx* c) {
   if (!c) return;
   if (c->st) cudaStreamSynchronize(c->st);
+  c->drain();
+  for (cudaEvent_t e : c->evpool) cudaEventDestroy(e);
   for (void* v : c->allocs) cudaFree(v);
   if (c->h_pinned) cudaFreeHost(c->h_pinned);
   if (c->h_count) cudaFreeHost(c->h_count);
@@ -707,6 +799,7 @@ void kkt(pint_ctx* c, const double* x, double* y) {
   a.conv = c->conv;
   a.x = x;
   a.y = y;
+  PROF(c, PINT_PROF_KKT_MV, 2);
   launch_kkt_matvec(a, c->st);
 }
 
@@ -717,8 +810,13 @@ void apply_prec(pint_ctx* c, const double* r, double* z, int* its) {
     c->e64.apply(r, z, its);
 }
 
+inline int mdot_kernels(int cnt) { return 2 * ((cnt + 7) / 8); }
+
 double dot_dev(pint_ctx* c, const double* a, const double* b, long long n) {
-  launch_mdot(a, 1, b, n, c->opart, c->oh, c->st);
+  {
+    PROF(c, PINT_PROF_OUTER, mdot_kernels(1));
+    launch_mdot(a, 1, b, n, c->opart, c->oh, c->st);
+  }
   cudaMemcpyAsync(c->h_pinned, c->oh, sizeof(double), cudaMemcpyDeviceToHost, c->st);
   cudaStreamSynchronize(c->st);
   return c->h_pinned[0];
@@ -746,13 +844,19 @@ pint_status fgmres(pint_ctx* c, double* x, pint_solve_info* info) {
   }
   // r = b - A x
   kkt(c, x, c->ot);
-  launch_axpby(1.0, c->ob, -1.0, c->ot, n, st);
+  {
+    PROF(c, PINT_PROF_OUTER, 1);
+    launch_axpby(1.0, c->ob, -1.0, c->ot, n, st);
+  }
   double beta = std::sqrt(dot_dev(c, c->ot, c->ot, n));
   double relres = beta / bnorm;
   int total = 0;
   std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), y(m);
   while (total < c->p.outer_maxit && relres > c->p.outer_tol) {
-    launch_axpby(1.0 / beta, c->ot, 0.0, c->oV, n, st);
+    {
+      PROF(c, PINT_PROF_OUTER, 1);
+      launch_axpby(1.0 / beta, c->ot, 0.0, c->oV, n, st);
+    }
     std::fill(g.begin(), g.end(), 0.0);
     g[0] = beta;
     int k = 0;
@@ -773,17 +877,24 @@ pint_status fgmres(pint_ctx* c, double* x, pint_solve_info* info) {
       cudaStreamSynchronize(st);
       auto a2 = now();
       // CGS2
+      {
+        PROF(c, PINT_PROF_OUTER, 2 * mdot_kernels(i + 1) + 2 + mdot_kernels(1));
       launch_mdot(c->oV, i + 1, Vn, n, c->opart, c->oh, st);
       launch_maxpy(c->oV, i + 1, c->oh, Vn, n, st);
       launch_mdot(c->oV, i + 1, Vn, n, c->opart, c->oh + (i + 1), st);
       launch_maxpy(c->oV, i + 1, c->oh + (i + 1), Vn, n, st);
       launch_mdot(Vn, 1, Vn, n, c->opart, c->oh + 2 * (i + 1), st);
+      }
       cudaMemcpyAsync(c->h_pinned, c->oh, sizeof(double) * (2 * (i + 1) + 1), cudaMemcpyDeviceToHost, st);
       if (!c->cu(cudaStreamSynchronize(st), "FGMRES iteration")) return PINT_ERR_CUDA;
+      c->drain();
       const double hn = std::sqrt(std::max(0.0, c->h_pinned[2 * (i + 1)]));
       for (int l = 0; l <= i; ++l) H[(size_t)l * m + i] = c->h_pinned[l] + c->h_pinned[i + 1 + l];
       H[(size_t)(i + 1) * m + i] = hn;
-      if (hn != 0.0) launch_axpby(1.0 / hn, Vn, 0.0, Vn, n, st);
+      if (hn != 0.0) {
+        PROF(c, PINT_PROF_OUTER, 1);
+        launch_axpby(1.0 / hn, Vn, 0.0, Vn, n, st);
+      }
       auto a3 = now();
       t_prec += ms(a0, a1);
       t_mv += ms(a1, a2);
@@ -812,9 +923,15 @@ pint_status fgmres(pint_ctx* c, double* x, pint_solve_info* info) {
     }
     for (int l = 0; l < k; ++l) c->h_pinned[l] = -y[l];
     cudaMemcpyAsync(c->oh, c->h_pinned, sizeof(double) * k, cudaMemcpyHostToDevice, st);
-    launch_maxpy(c->oZ, k, c->oh, x, n, st);  // x += Z y
+    {
+      PROF(c, PINT_PROF_OUTER, 1);
+      launch_maxpy(c->oZ, k, c->oh, x, n, st);  // x += Z y
+    }
     kkt(c, x, c->ot);
-    launch_axpby(1.0, c->ob, -1.0, c->ot, n, st);
+    {
+      PROF(c, PINT_PROF_OUTER, 1);
+      launch_axpby(1.0, c->ob, -1.0, c->ot, n, st);
+    }
     beta = std::sqrt(dot_dev(c, c->ot, c->ot, n));
     relres = beta / bnorm;
     inf.restarts++;
@@ -984,7 +1101,7 @@ pint_status pint_kkt_matvec(pint_handle h, const double* x, double* y) {
   const size_t n = (size_t)h->K * h->s.nblk;
   if (!h->cu(cudaMemcpyAsync(h->ox, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->st), "copy x"))
     return PINT_ERR_CUDA;
-  launch_mask_blocks(h->s, h->K, 1, h->ox, h->st);
+  { PROF(h, PINT_PROF_OTHER, 1); launch_mask_blocks(h->s, h->K, 1, h->ox, h->st); }
   kkt(h, h->ox, y);
   return h->launched("kkt matvec") ? PINT_OK : PINT_ERR_CUDA;
 }
@@ -997,7 +1114,7 @@ pint_status pint_apply_preconditioner(pint_handle h, const double* r, double* z)
   const size_t n = (size_t)h->K * h->s.nblk;
   if (!h->cu(cudaMemcpyAsync(h->ot, r, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->st), "copy r"))
     return PINT_ERR_CUDA;
-  launch_mask_blocks(h->s, h->K, 1, h->ot, h->st);
+  { PROF(h, PINT_PROF_OTHER, 1); launch_mask_blocks(h->s, h->K, 1, h->ot, h->st); }
   apply_prec(h, h->ot, z, nullptr);
   return h->launched("preconditioner") ? PINT_OK : PINT_ERR_CUDA;
 }
@@ -1011,7 +1128,7 @@ pint_status pint_solve(pint_handle h, double* x, pint_solve_info* info) {
   const size_t n = (size_t)h->K * h->s.nblk;
   if (!h->cu(cudaMemcpyAsync(h->ox, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->st), "copy x0"))
     return PINT_ERR_CUDA;
-  launch_mask_blocks(h->s, h->K, 1, h->ox, h->st);
+  { PROF(h, PINT_PROF_OTHER, 1); launch_mask_blocks(h->s, h->K, 1, h->ox, h->st); }
   pint_status rc = fgmres(h, h->ox, info);
   if (!h->cu(cudaMemcpyAsync(x, h->ox, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->st), "copy x") ||
       !h->cu(cudaStreamSynchronize(h->st), "solve"))
@@ -1028,7 +1145,7 @@ pint_status pint_solve_host(pint_handle h, double* x_host, pint_solve_info* info
   const size_t n = (size_t)h->K * h->s.nblk;
   if (!h->cu(cudaMemcpyAsync(h->ox, x_host, sizeof(double) * n, cudaMemcpyHostToDevice, h->st), "upload x0"))
     return PINT_ERR_CUDA;
-  launch_mask_blocks(h->s, h->K, 1, h->ox, h->st);
+  { PROF(h, PINT_PROF_OTHER, 1); launch_mask_blocks(h->s, h->K, 1, h->ox, h->st); }
   pint_status rc = fgmres(h, h->ox, info);
   if (!h->cu(cudaMemcpyAsync(x_host, h->ox, sizeof(double) * n, cudaMemcpyDeviceToHost, h->st), "download x") ||
       !h->cu(cudaStreamSynchronize(h->st), "solve"))
@@ -1065,7 +1182,7 @@ template <class T>
 pint_status dft_fwd_T(pint_ctx* c, Engine<T>& e, const double* x, double* xhat) {
   const size_t n = (size_t)c->K * c->s.nblk;
   cudaMemcpyAsync(c->ot, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->st);
-  launch_mask_blocks(c->s, c->K, 1, c->ot, c->st);
+  { PROF(c, PINT_PROF_OTHER, 1); launch_mask_blocks(c->s, c->K, 1, c->ot, c->st); }
   launch_dft_forward<T>(c->K, c->J, c->s.nblk, c->ot, e.R, e.cosk, e.sink, c->st);
   from_T<T>(c, e.R, xhat, (size_t)c->J * c->s.nblk);
   return c->launched("dft forward") ? PINT_OK : PINT_ERR_CUDA;
@@ -1076,7 +1193,7 @@ pint_status dft_inv_T(pint_ctx* c, Engine<T>& e, const double* xhat, double* x) 
   const size_t fl = (size_t)c->J * c->s.nblk;
   to_T<T>(c, xhat, e.R, fl);
   launch_dft_inverse<T>(c->K, c->J, c->s.nblk, e.R, x, e.cosk, e.sink, c->st);
-  launch_mask_blocks(c->s, c->K, 1, x, c->st);
+  { PROF(c, PINT_PROF_OTHER, 1); launch_mask_blocks(c->s, c->K, 1, x, c->st); }
   return c->launched("dft inverse") ? PINT_OK : PINT_ERR_CUDA;
 }
 
@@ -1085,7 +1202,7 @@ pint_status freq_in(pint_ctx* c, Engine<T>& e, const double* in) {
   // copy, zero the non-unknown entries in FP64, then convert to T
   const size_t fl = (size_t)c->J * c->s.nblk;
   cudaMemcpyAsync(c->ofreq, in, sizeof(double) * 2 * fl, cudaMemcpyDeviceToDevice, c->st);
-  launch_mask_blocks(c->s, c->J, 2, c->ofreq, c->st);
+  { PROF(c, PINT_PROF_OTHER, 1); launch_mask_blocks(c->s, c->J, 2, c->ofreq, c->st); }
   to_T<T>(c, c->ofreq, e.R, fl);
   return PINT_OK;
 }
@@ -1201,6 +1318,30 @@ pint_status pint_component_apply(pint_handle h, int which, int j, const double* 
   if (j < 0 || j >= h->J) return h->fail(PINT_ERR_ARG, "frequency index out of range");
   return h->fp32 ? component_T<float>(h, h->e32, which, j, in, out)
                  : component_T<double>(h, h->e64, which, j, in, out);
+}
+
+pint_status pint_profile_enable(pint_handle h, unsigned mask) {
+  if (!h) return g_err = "null handle", PINT_ERR_ARG;
+  if (!h->cu(cudaStreamSynchronize(h->st), "profile enable")) return PINT_ERR_CUDA;
+  h->drain();
+  h->prof_mask = mask;
+  for (int i = 0; i < PINT_PROF_CLASSES; ++i) {
+    h->prof_launch[i] = h->prof_timed[i] = 0;
+    h->prof_ms[i] = 0.0;
+  }
+  return PINT_OK;
+}
+
+pint_status pint_profile_read(pint_handle h, pint_profile* out) {
+  if (!h || !out) return g_err = "null argument", PINT_ERR_ARG;
+  if (!h->cu(cudaStreamSynchronize(h->st), "profile read")) return PINT_ERR_CUDA;
+  h->drain();
+  for (int i = 0; i < PINT_PROF_CLASSES; ++i) {
+    out->launches[i] = h->prof_launch[i];
+    out->timed[i] = h->prof_timed[i];
+    out->ms[i] = h->prof_ms[i];
+  }
+  return PINT_OK;
 }
 
 const char* pint_last_error(pint_handle h) {
