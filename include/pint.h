@@ -195,6 +195,24 @@ pint_status pint_freq_block_solve(pint_handle h, const double* rhat_dev, double*
 pint_status pint_component_apply(pint_handle h, int which, int j, const double* in_dev,
                                  double* out_dev);
 
+/* Multigrid solve on one field, like pint_component_apply with which = 0..3,
+ * but without allocating anything: no device or host memory is allocated or
+ * freed, by this library or any library it calls.  No counterpart in the
+ * paper; it exists for callers that cannot call cudaMalloc while they run --
+ * for example an application whose memory pool already reserved the device
+ * memory, or a latency-critical loop where an allocation would synchronise
+ * the device.
+ * Scratch comes from one fixed 2 MiB array in device memory that every GPU
+ * loading this library keeps until the process exits; a field whose scratch
+ * does not fit (staged input, output and V-cycle levels: about N <= 64 for
+ * velocity fields) is rejected with PINT_ERR_ARG and a message giving the
+ * bytes needed.  The first call on a device looks up the array's device
+ * address (make that first call before any stream capture).  All calls
+ * share the array: calls that overlap on the GPU race.  Inputs and outputs
+ * as in pint_component_apply (complex FP64, full grid, caller-owned);
+ * the device current at the call must be the handle's device. */
+pint_status pint_mg_apply_noalloc(pint_handle h, int which, int j, const double* in_dev, double* out_dev);
+
 /* ---- tracing ------------------------------------------------------------
  * Kernel classes of the hot path.  Launch counts are always kept; CUDA-event
  * timing (events recorded on the handle's stream around each launch of a

@@ -77,6 +77,7 @@ _SIGS = {
     "pint_freq_block_matvec": (ctypes.c_int, [_P, _P, _P]),
     "pint_freq_block_solve": (ctypes.c_int, [_P, _P, _P, _P]),
     "pint_component_apply": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P, _P]),
+    "pint_mg_apply_noalloc": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P, _P]),
     "pint_profile_enable": (ctypes.c_int, [_P, ctypes.c_uint]),
     "pint_profile_read": (ctypes.c_int, [_P, ctypes.POINTER(Profile)]),
     "pint_last_error": (ctypes.c_char_p, [_P]),
@@ -236,6 +237,12 @@ class Problem:
         _check(lib().pint_freq_block_solve(self.h, _dptr(rhat, "complex128", self.freq_len),
                                            _dptr(yhat, "complex128", self.freq_len), its), self.h)
         return list(its)
+
+    def mg_apply_noalloc(self, which, j, x, y):
+        """Multigrid on one field with the library's fixed scratch array (no allocation)."""
+        w = COMPONENT[which] if isinstance(which, str) else int(which)
+        _check(lib().pint_mg_apply_noalloc(self.h, w, j, _dptr(x, "complex128"), _dptr(y, "complex128")),
+               self.h)
 
     def profile_enable(self, classes=()):
         """Reset the counters; time the named kernel classes with CUDA events."""

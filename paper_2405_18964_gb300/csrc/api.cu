@@ -14,6 +14,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <mutex>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -1350,3 +1351,130 @@ const char* pint_last_error(pint_handle h) {
 }
 
 }  // extern "C"
+
+// ============================================================================
+// Multigrid component solve without allocation (pint_mg_apply_noalloc).
+//
+// Scratch for this entry point lives in one file-scope device array instead
+// of the handle's workspace: the staged input field, the output field, the
+// per-level V-cycle arrays and the job descriptor.  Every GPU that loads the
+// library holds the array until the process exits.  Its device address is
+// looked up once per device (cudaGetSymbolAddress, with that device current)
+// on the first call there; host code never hands the array's name to a
+// kernel.  All calls share the array: calls that overlap on the GPU (other
+// streams, other threads) race on it.
+// ============================================================================
+namespace {
+
+constexpr size_t NOALLOC_SCRATCH_BYTES = size_t(2) << 20;  // 2 MiB
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
+
+constexpr int NOALLOC_MAX_DEVICES = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {};
+
+// Device address of the scratch array on the current device (set-up on first use).
+cudaError_t noalloc_scratch(void** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return cudaSuccess;
+}
+
+__global__ void noalloc_write_job(FieldJob* dst, FieldJob job) { *dst = job; }
+
+template <class T>
+__global__ void noalloc_stage_in(const double* in, cpx<T>* dst, int n, int space) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n * n) return;
+  const int ix = q % n, iy = q / n;
+  const bool unk = space == 2 ? (ix > 0 && iy > 0 && ix < n - 1 && iy < n - 1) : ((ix | iy) != 0);
+  dst[q] = unk ? mkc<T>(T(in[2 * q]), T(in[2 * q + 1])) : czero<T>();
+}
+
+template <class T>
+__global__ void noalloc_stage_out(const cpx<T>* src, double* out, int len) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= len) return;
+  out[2 * q] = (double)src[q].x;
+  out[2 * q + 1] = (double)src[q].y;
+}
+
+inline size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+
+template <class T>
+pint_status mg_noalloc_T(pint_ctx* c, Engine<T>& e, int which, int j, const double* in, double* out) {
+  const Slots& s = c->s;
+  const int J = c->J;
+  const int space = which == 3 ? 1 : 2;
+  int op;
+  if (which == 0) {
+    if (c->oseen) return c->fail(PINT_ERR_ARG, "W_j exists for Stokes problems only");
+    op = j;
+  } else if (which == 1 || which == 2) {
+    if (!c->oseen) return c->fail(PINT_ERR_ARG, "Q_j exists for Oseen problems only");
+    op = which == 1 ? j : J + j;
+  } else {
+    op = 2 * J;
+  }
+  const MGLayout& lay = space == 2 ? c->lay2 : c->lay1;
+  const int n = space == 2 ? s.n2 : s.n1;
+  const size_t field = (size_t)n * n * sizeof(cpx<T>);
+  const size_t need = align256(sizeof(FieldJob)) + 2 * align256(field) + align256((size_t)lay.per_job * sizeof(cpx<T>));
+  if (need > NOALLOC_SCRATCH_BYTES)
+    return c->fail(PINT_ERR_ARG, "pint_mg_apply_noalloc: this field needs " + std::to_string(need) +
+                                     " bytes of scratch, more than the fixed " +
+                                     std::to_string(NOALLOC_SCRATCH_BYTES) + " bytes");
+  void* base = nullptr;
+  if (!c->cu(noalloc_scratch(&base), "pint_mg_apply_noalloc scratch set-up")) return PINT_ERR_CUDA;
+  unsigned char* p = static_cast<unsigned char*>(base);
+  FieldJob* job = reinterpret_cast<FieldJob*>(p);
+  p += align256(sizeof(FieldJob));
+  cpx<T>* bfield = reinterpret_cast<cpx<T>*>(p);
+  p += align256(field);
+  cpx<T>* xfield = reinterpret_cast<cpx<T>*>(p);
+  p += align256(field);
+  cpx<T>* ws = reinterpret_cast<cpx<T>*>(p);
+
+  noalloc_write_job<<<1, 1, 0, c->st>>>(job, FieldJob{0, 0, op, 0});
+  noalloc_stage_in<T><<<(n * n + 255) / 256, 256, 0, c->st>>>(in, bfield, n, space);
+  MGLaunch<T> L{};
+  L.tabs = e.tabs;
+  L.lay = lay;
+  L.ops = c->d_ops;
+  L.coarse_inv = c->d_cinv;
+  L.jobs = job;
+  L.njobs = 1;
+  L.xbase = xfield;
+  L.bbase = bfield;
+  L.ws = ws;
+  L.active = nullptr;
+  L.cycles = c->p.mg_cycles;
+  L.pre = c->p.mg_pre;
+  L.post = c->p.mg_post;
+  L.omega = c->p.sor_omega;
+  L.space = space;
+  L.conv = (which == 1 || which == 2) ? c->conv : false;
+  launch_mg<T>(L, c->st);
+  noalloc_stage_out<T><<<(n * n + 255) / 256, 256, 0, c->st>>>(xfield, out, n * n);
+  return c->launched("pint_mg_apply_noalloc") ? PINT_OK : PINT_ERR_CUDA;
+}
+
+}  // namespace
+
+extern "C" pint_status pint_mg_apply_noalloc(pint_handle h, int which, int j, const double* in, double* out) {
+  if (!h || !in || !out) return g_err = "null argument", PINT_ERR_ARG;
+  if (which < 0 || which > 3) return h->fail(PINT_ERR_ARG, "which must be a multigrid operator (0..3)");
+  if (j < 0 || j >= h->J) return h->fail(PINT_ERR_ARG, "frequency index out of range");
+  return h->fp32 ? mg_noalloc_T<float>(h, h->e32, which, j, in, out)
+                 : mg_noalloc_T<double>(h, h->e64, which, j, in, out);
+}
