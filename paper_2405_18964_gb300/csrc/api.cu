@@ -60,8 +60,11 @@ struct Engine {
   T* cosk = nullptr;
   T* sink = nullptr;
 
-  void mg(int space, bool conv, const FieldJob* jobs, int njobs, cpx<T>* xb, const cpx<T>* bb, const int* active);
-  void cheb(int space, const FieldJob* jobs, int njobs, cpx<T>* xb, const cpx<T>* bb, const int* active);
+  const T* n2d[PINT_MAXLEV] = {};  // per-level Q2 convection stencils (conv only)
+  void mg(int space, bool conv, const FieldJob* jobs, int njobs, cpx<T>* xb, const cpx<T>* bb, const int* active,
+          int fields_per_job = 2);
+  void cheb(int space, const FieldJob* jobs, int njobs, cpx<T>* xb, const cpx<T>* bb, const int* active,
+            int fields_per_job = 2);
   void block_prec(const cpx<T>* U, cpx<T>* Out, const int* active);
   void block_matvec(const BlkCoef* coef, const cpx<T>* X, cpx<T>* Out, const int* active);
   void inner_solve(const cpx<T>* S, cpx<T>* X, int* its_host);
@@ -226,9 +229,13 @@ Tabs<float>& tabs_of<float>(pint_ctx* c) {
 
 template <class T>
 void Engine<T>::mg(int space, bool conv, const FieldJob* jobs, int njobs, cpx<T>* xb, const cpx<T>* bb,
-                   const int* active) {
+                   const int* active, int fields_per_job) {
   MGLaunch<T> L{};
   L.tabs = tabs;
+  L.t64 = c->t64;
+  for (int l = 0; l < PINT_MAXLEV; ++l) L.n2d[l] = n2d[l];
+  L.fields_per_job = fields_per_job;
+  L.cw = c->oseen && space == 2;
   L.lay = space == 2 ? c->lay2 : c->lay1;
   L.ops = c->d_ops;
   L.coarse_inv = c->d_cinv;
@@ -249,9 +256,12 @@ void Engine<T>::mg(int space, bool conv, const FieldJob* jobs, int njobs, cpx<T>
 }
 
 template <class T>
-void Engine<T>::cheb(int space, const FieldJob* jobs, int njobs, cpx<T>* xb, const cpx<T>* bb, const int* active) {
+void Engine<T>::cheb(int space, const FieldJob* jobs, int njobs, cpx<T>* xb, const cpx<T>* bb, const int* active,
+                     int fields_per_job) {
   ChebLaunch<T> L{};
   L.tabs = tabs;
+  L.t64 = c->t64;
+  L.fields_per_job = fields_per_job;
   L.jobs = jobs;
   L.njobs = njobs;
   L.xbase = xb;
@@ -292,10 +302,10 @@ void Engine<T>::block_prec(const cpx<T>* U, cpx<T>* Out, const int* active) {
   cudaStream_t st = c->st;
   if (!c->oseen) {
     // W_j^{-1} on the four velocity fields (v and lambda blocks)
-    mg(2, false, c->j_W4, 4 * J, Out, U, active);
+    mg(2, false, c->j_W4, 4 * J, Out, U, active, 1);
     // S^_j^{-1} = (1 + c1) K_p^{-1} + nu c2 M_p^{-1} on the p and mu blocks
-    mg(1, false, c->j_Kp2, 2 * J, T1, U, active);
-    cheb(1, c->j_Mp2, 2 * J, T2, U, active);
+    mg(1, false, c->j_Kp2, 2 * J, T1, U, active, 1);
+    cheb(1, c->j_Mp2, J, T2, U, active);
     { PROF(c, PINT_PROF_COMBO, 1); launch_lincomb<T>(J, s.nblk, s.nq, Out, s.p, T1, s.p, c->d_sa, T2, s.p, c->d_sb, active, st); }
     { PROF(c, PINT_PROF_COMBO, 1); launch_lincomb<T>(J, s.nblk, s.nq, Out, s.mu, T1, s.mu, c->d_sa, T2, s.mu, c->d_sb, active, st); }
     return;
@@ -322,7 +332,7 @@ void Engine<T>::block_prec(const cpx<T>* U, cpx<T>* Out, const int* active) {
     ca.out = T1;
     { PROF(c, PINT_PROF_COMBO, 1); launch_combo<T>(ca, st); }
     // x1 += (1/tau) M^-1 T1[v]   (M^ = Chebyshev)
-    cheb(2, c->j_M2, 2 * J, T2, T1, active);
+    cheb(2, c->j_M2, J, T2, T1, active);
     { PROF(c, PINT_PROF_COMBO, 1); launch_lincomb<T>(J, s.nblk, lenv, Out, s.vx, Out, s.vx, c->d_one, T2, s.vx, c->d_invtau, active, st); }
     // T1[lam] = b2 - (d M + tau L) x1 + tau/beta M x2
     ca.coef = c->d_cuzd;
@@ -333,7 +343,7 @@ void Engine<T>::block_prec(const cpx<T>* U, cpx<T>* Out, const int* active) {
     ca.out = T1;
     { PROF(c, PINT_PROF_COMBO, 1); launch_combo<T>(ca, st); }
     // S^^{-1} = tau Q^{-H} M Q^{-1}
-    mg(2, c->conv, c->j_Q2, 2 * J, T2, T1, active);
+    mg(2, c->conv, c->j_Q2, 2 * J, T2, T1, active, 1);
     ca.coef = c->d_cmass;
     ca.ncoef = 2;
     ca.rows[0] = ComboRow{s.lx, 0, {s.lx, 0}, 0, {1, 0}, 1, 0};
@@ -342,7 +352,7 @@ void Engine<T>::block_prec(const cpx<T>* U, cpx<T>* Out, const int* active) {
     ca.z = nullptr;
     ca.out = T3;
     { PROF(c, PINT_PROF_COMBO, 1); launch_combo<T>(ca, st); }
-    mg(2, c->conv, c->j_QH2, 2 * J, T1, T3, active);
+    mg(2, c->conv, c->j_QH2, 2 * J, T1, T3, active, 1);
     // x2 -= (1/mu) tau Q^{-H} M Q^{-1} (...)
     { PROF(c, PINT_PROF_COMBO, 1); launch_lincomb<T>(J, s.nblk, lenv, Out, s.lx, Out, s.lx, c->d_one, T1, s.lx, c->d_mtaumu, active, st); }
   }
@@ -367,7 +377,7 @@ void Engine<T>::block_prec(const cpx<T>* U, cpx<T>* Out, const int* active) {
     launch_bres<T>(br, st);
   }
   // swap + (tau M_p)^{-1}: T2[p] = Cheb(T1[mu]), T2[mu] = Cheb(T1[p]) (1/tau folded below)
-  cheb(1, c->j_Mp2s, 2 * J, T2, T1, active);
+  cheb(1, c->j_Mp2s, J, T2, T1, active);
   // X_p, the second swap's sign and the 1/tau factors
   ComboArgs<T> cq{};
   cq.tabs = tabs;
@@ -386,7 +396,7 @@ void Engine<T>::block_prec(const cpx<T>* U, cpx<T>* Out, const int* active) {
   cq.out = T3;
   { PROF(c, PINT_PROF_COMBO, 1); launch_combo<T>(cq, st); }
   // swap + (tau K_p)^{-1}: Out[p] = MG(T3[mu]), Out[mu] = MG(T3[p])
-  mg(1, false, c->j_Kp2s, 2 * J, Out, T3, active);
+  mg(1, false, c->j_Kp2s, 2 * J, Out, T3, active, 1);
 }
 
 // Inner solve on all frequencies: GMRES(A_j, P_j, S_j, eps) or, for the
@@ -527,6 +537,14 @@ bool setup_engine(pint_ctx* c, Engine<T>& e, size_t mg_jobs_q2, size_t mg_jobs_q
   const size_t mgws = std::max(mg_jobs_q2 * (size_t)c->lay2.per_job, mg_jobs_q1 * (size_t)c->lay1.per_job);
   const size_t chws = std::max(cheb_jobs_q2 * (size_t)c->cheb_per_q2, cheb_jobs_q1 * (size_t)c->cheb_per_q1);
   if (!c->alloc(&e.mgws, mgws * sizeof(cpx<T>)) || !c->alloc(&e.chebws, chws * sizeof(cpx<T>))) return false;
+  if (c->conv)
+    for (int l = 0; l < c->nlev; ++l) {
+      const size_t n2 = 2 * (size_t)(c->N >> l) + 1, w6 = (n2 + 5) / 6;
+      T* t = nullptr;
+      if (!c->alloc(&t, 36 * w6 * w6 * 25 * sizeof(T))) return false;
+      launch_build_n2d<T>(c->t64, l, t, c->st);
+      e.n2d[l] = t;
+    }
   std::vector<T> cs(c->K), sn(c->K);
   for (int k = 0; k < c->K; ++k) {
     const double a = 2.0 * M_PI * (double)k / (double)c->K;
@@ -544,8 +562,17 @@ MGLayout make_layout(int nlev, int N, int space) {
     const int Nl = N >> l;
     L.n[l] = space == 2 ? 2 * Nl + 1 : Nl + 1;
   }
-  for (int l = 1; l < nlev; ++l) {
-    const long long sz = (long long)L.n[l] * L.n[l];
+  // Q2 fields run in the class-blocked layout (36 classes of ceil(n/6)^2
+  // nodes), so level 0 is copied too
+  auto lsize = [&](int l) -> long long {
+    if (space == 2) {
+      const long long w6 = (L.n[l] + 5) / 6;
+      return 36 * w6 * w6;
+    }
+    return (long long)L.n[l] * L.n[l];
+  };
+  for (int l = space == 2 ? 0 : 1; l < nlev; ++l) {
+    const long long sz = lsize(l);
     L.off_x[l] = off;
     off += sz;
     L.off_b[l] = off;
@@ -553,7 +580,7 @@ MGLayout make_layout(int nlev, int N, int space) {
   }
   for (int l = 0; l + 1 < nlev; ++l) {
     L.off_r[l] = off;
-    off += (long long)L.n[l] * L.n[l];
+    off += lsize(l);
   }
   L.per_job = off > 0 ? off : 1;
   return L;
@@ -709,25 +736,35 @@ pint_status build(pint_ctx* c) {
     return c->fail(PINT_ERR_OOM, "device allocation failed (coefficients)");
 
   // ---- job tables
-  auto jobs = [&](std::initializer_list<std::pair<long long, long long>> sl, int opbase, bool per_j_op) {
+  // each job: the (x slot, b slot) pairs of one frequency sharing one operator
+  using SlotPairs = std::vector<std::pair<long long, long long>>;
+  auto jobs = [&](std::vector<SlotPairs> groups, int opbase, bool per_j_op) {
     std::vector<FieldJob> v;
     for (int j = 0; j < J; ++j)
-      for (auto& xb : sl)
-        v.push_back(FieldJob{(long long)j * s.nblk + xb.first, (long long)j * s.nblk + xb.second,
-                             per_j_op ? opbase + j : opbase, j});
+      for (auto& grp : groups) {
+        FieldJob jb{};
+        jb.nf = (int)grp.size();
+        for (int f = 0; f < jb.nf; ++f) {
+          jb.x_off[f] = (long long)j * s.nblk + grp[f].first;
+          jb.b_off[f] = (long long)j * s.nblk + grp[f].second;
+        }
+        jb.op = per_j_op ? opbase + j : opbase;
+        jb.freq = j;
+        v.push_back(jb);
+      }
     return v;
   };
   bool ok = true;
   if (!c->oseen) {
-    ok = ok && c->upload(&c->j_W4, jobs({{s.vx, s.vx}, {s.vy, s.vy}, {s.lx, s.lx}, {s.ly, s.ly}}, 0, true));
-    ok = ok && c->upload(&c->j_Kp2, jobs({{s.p, s.p}, {s.mu, s.mu}}, 2 * J, false));
-    ok = ok && c->upload(&c->j_Mp2, jobs({{s.p, s.p}, {s.mu, s.mu}}, 2 * J + 2, false));
+    ok = ok && c->upload(&c->j_W4, jobs({{{s.vx, s.vx}}, {{s.vy, s.vy}}, {{s.lx, s.lx}}, {{s.ly, s.ly}}}, 0, true));
+    ok = ok && c->upload(&c->j_Kp2, jobs({{{s.p, s.p}}, {{s.mu, s.mu}}}, 2 * J, false));
+    ok = ok && c->upload(&c->j_Mp2, jobs({{{s.p, s.p}, {s.mu, s.mu}}}, 2 * J + 2, false));
   } else {
-    ok = ok && c->upload(&c->j_Q2, jobs({{s.lx, s.lx}, {s.ly, s.ly}}, 0, true));
-    ok = ok && c->upload(&c->j_QH2, jobs({{s.lx, s.lx}, {s.ly, s.ly}}, J, true));
-    ok = ok && c->upload(&c->j_M2, jobs({{s.vx, s.vx}, {s.vy, s.vy}}, 2 * J + 1, false));
-    ok = ok && c->upload(&c->j_Kp2s, jobs({{s.p, s.mu}, {s.mu, s.p}}, 2 * J, false));
-    ok = ok && c->upload(&c->j_Mp2s, jobs({{s.p, s.mu}, {s.mu, s.p}}, 2 * J + 2, false));
+    ok = ok && c->upload(&c->j_Q2, jobs({{{s.lx, s.lx}}, {{s.ly, s.ly}}}, 0, true));
+    ok = ok && c->upload(&c->j_QH2, jobs({{{s.lx, s.lx}}, {{s.ly, s.ly}}}, J, true));
+    ok = ok && c->upload(&c->j_M2, jobs({{{s.vx, s.vx}, {s.vy, s.vy}}}, 2 * J + 1, false));
+    ok = ok && c->upload(&c->j_Kp2s, jobs({{{s.p, s.mu}}, {{s.mu, s.p}}}, 2 * J, false));
+    ok = ok && c->upload(&c->j_Mp2s, jobs({{{s.p, s.mu}, {s.mu, s.p}}}, 2 * J + 2, false));
   }
   ok = ok && c->alloc(&c->j_one, sizeof(FieldJob)) && c->alloc(&c->d_active_one, sizeof(int) * J);
   if (!ok) return c->fail(PINT_ERR_OOM, "device allocation failed (jobs)");
@@ -737,9 +774,10 @@ pint_status build(pint_ctx* c) {
   c->lay1 = make_layout(c->nlev, N, 1);
   c->cheb_per_q2 = 2LL * s.ns;
   c->cheb_per_q1 = 2LL * s.nq;
+  // workspace slots: jobs x 2 fields per job
   const size_t mgq2 = c->oseen ? 2 * (size_t)J : 4 * (size_t)J;
   const size_t mgq1 = 2 * (size_t)J;
-  const size_t chq2 = c->oseen ? 2 * (size_t)J : 1;
+  const size_t chq2 = c->oseen ? 2 * (size_t)J : 2;
   const size_t chq1 = 2 * (size_t)J;
 
   // ---- inner GMRES state
@@ -1279,12 +1317,14 @@ pint_status component_T(pint_ctx* c, Engine<T>& e, int which, int j, const doubl
   double* stage = c->ot;  // FP64 scratch of kkt_len >= 2 * len doubles
   cudaMemcpyAsync(stage, hin.data(), sizeof(double) * 2 * len, cudaMemcpyHostToDevice, c->st);
   to_T<T>(c, stage, e.T1, len);
-  FieldJob jb{0, 0, op, 0};
+  FieldJob jb{};
+  jb.nf = 1;
+  jb.op = op;
   cudaMemcpyAsync(c->j_one, &jb, sizeof(FieldJob), cudaMemcpyHostToDevice, c->st);
   if (which <= 3)
-    e.mg(space, which == 1 || which == 2 ? c->conv : false, c->j_one, 1, e.T2, e.T1, nullptr);
+    e.mg(space, which == 1 || which == 2 ? c->conv : false, c->j_one, 1, e.T2, e.T1, nullptr, 1);
   else
-    e.cheb(space, c->j_one, 1, e.T2, e.T1, nullptr);
+    e.cheb(space, c->j_one, 1, e.T2, e.T1, nullptr, 1);
   from_T<T>(c, e.T2, out, len);
   return c->launched("component") && c->cu(cudaStreamSynchronize(c->st), "component") ? PINT_OK : PINT_ERR_CUDA;
 }
@@ -1445,10 +1485,17 @@ pint_status mg_noalloc_T(pint_ctx* c, Engine<T>& e, int which, int j, const doub
   p += align256(field);
   cpx<T>* ws = reinterpret_cast<cpx<T>*>(p);
 
-  noalloc_write_job<<<1, 1, 0, c->st>>>(job, FieldJob{0, 0, op, 0});
+  FieldJob one{};
+  one.nf = 1;
+  one.op = op;
+  noalloc_write_job<<<1, 1, 0, c->st>>>(job, one);
   noalloc_stage_in<T><<<(n * n + 255) / 256, 256, 0, c->st>>>(in, bfield, n, space);
   MGLaunch<T> L{};
   L.tabs = e.tabs;
+  L.t64 = c->t64;
+  for (int l = 0; l < PINT_MAXLEV; ++l) L.n2d[l] = e.n2d[l];
+  L.fields_per_job = 1;
+  L.cw = c->oseen && space == 2;
   L.lay = lay;
   L.ops = c->d_ops;
   L.coarse_inv = c->d_cinv;

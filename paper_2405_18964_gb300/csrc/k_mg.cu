@@ -21,21 +21,88 @@
 
 namespace pint {
 
-constexpr int MG_THREADS = 512;
+constexpr int MG_THREADS = 256;
+constexpr int MG_MINB = 4;  // resident CTAs per SM the register budget targets
 
+// ----------------------------------------------------------------------------
+// Stencil weights.  On the uniform grid the 2-D weights of a constant-
+// coefficient operator a M + b K depend only on the node type: for Q2 the
+// parities of (ix, iy) (vertex / midpoint), for Q1 whether ix, iy lie on the
+// boundary (natural conditions give half rows there).  They are formed in
+// FP64 from the 1-D bands and rounded once to T; the convection part (which
+// varies per node) comes from a per-node table built the same way.
+// ----------------------------------------------------------------------------
 template <int SP>
-__device__ __forceinline__ int nside(int N) { return SP == 2 ? 2 * N + 1 : N + 1; }
+__device__ __forceinline__ int ntypes() { return SP == 2 ? 4 : 9; }
+template <int SP>
+__device__ __forceinline__ int nstencil() { return SP == 2 ? 25 : 9; }
 
-// Colour-class geometry: first index and count along one axis.
+// representative node index along one axis for a node type coordinate
 template <int SP>
-__device__ __forceinline__ void colour_axis(int n, int cc, int& first, int& count) {
-  if (SP == 2) {  // interior nodes 1..n-2, stride 3
-    first = (cc == 0) ? 3 : cc;
-    count = (first <= n - 2) ? (n - 2 - first) / 3 + 1 : 0;
-  } else {  // all nodes 0..n-1, stride 2
-    first = cc;
-    count = (first <= n - 1) ? (n - 1 - first) / 2 + 1 : 0;
+__device__ __forceinline__ int type_rep(int t, int n) {
+  if (SP == 2) return t ? 1 : 2;           // midpoint : vertex
+  return t == 0 ? 0 : (t == 1 ? 1 : n - 1);  // left boundary : interior : right boundary
+}
+template <int SP>
+__device__ __forceinline__ int node_type(int ix, int iy, int n) {
+  if (SP == 2) return (ix & 1) + 2 * (iy & 1);
+  const int tx = ix == 0 ? 0 : (ix == n - 1 ? 2 : 1);
+  const int ty = iy == 0 ? 0 : (iy == n - 1 ? 2 : 1);
+  return tx + 3 * ty;
+}
+
+// sw[type][k] = a M + b K at level l (FP64 -> T), sdi[type] = 1 / diagonal.
+template <class T, int SP>
+__device__ void level_weights(const Tabs<double>& t64, int l, int n, cpx<double> a, double b, cpx<T>* sw,
+                              cpx<T>* sdi) {
+  constexpr int W = SP == 2 ? 5 : 3;
+  const double* tab = SP == 2 ? t64.q2[l] : t64.q1[l];
+  const int nt = ntypes<SP>(), ns = nstencil<SP>();
+  for (int q = threadIdx.x; q < nt * ns; q += blockDim.x) {
+    const int type = q / ns, k = q % ns;
+    const int dx = k % W, dy = k / W;
+    const int tx = SP == 2 ? (type & 1) : type % 3;
+    const int ty = SP == 2 ? (type >> 1) : type / 3;
+    const int ix = type_rep<SP>(tx, n), iy = type_rep<SP>(ty, n);
+    const double mx = tab[(size_t)(0 * n + ix) * W + dx], my = tab[(size_t)(0 * n + iy) * W + dy];
+    const double kx = tab[(size_t)(1 * n + ix) * W + dx], ky = tab[(size_t)(1 * n + iy) * W + dy];
+    const double m2 = mx * my, k2 = kx * my + mx * ky;
+    const cpx<double> w = mkc<double>(a.x * m2 + b * k2, a.y * m2);
+    sw[q] = mkc<T>(T(w.x), T(w.y));
+    if (k == ns / 2) {
+      const double den = w.x * w.x + w.y * w.y;
+      sdi[type] = mkc<T>(T(w.x / den), T(-w.y / den));
+    }
   }
+}
+
+// (A x) at a node: sum_k w_k x_k (+ c sum_k N_k x_k for convection).
+template <class T, int SP, bool CONV, bool CW>
+__device__ __forceinline__ cpx<T> stencil(const cpx<T>* __restrict__ w, const T* __restrict__ nrow, T c, int n,
+                                          int ix, int iy, const cpx<T>* __restrict__ x) {
+  constexpr int W = SP == 2 ? 5 : 3;
+  constexpr int H = W / 2;
+  int cols[W];
+#pragma unroll
+  for (int d = 0; d < W; ++d) cols[d] = clampi(ix + d - H, 0, n - 1);
+  cpx<T> acc = czero<T>(), accn = czero<T>();
+#pragma unroll
+  for (int dy = 0; dy < W; ++dy) {
+    const cpx<T>* row = x + (size_t)clampi(iy + dy - H, 0, n - 1) * n;
+#pragma unroll
+    for (int dx = 0; dx < W; ++dx) {
+      const cpx<T> v = row[cols[dx]];
+      const cpx<T> wk = w[dy * W + dx];
+      if (CW) {
+        acc = acc + wk * v;
+      } else {
+        rfma(acc, wk.x, v);
+      }
+      if (CONV) rfma(accn, nrow[dy * W + dx], v);
+    }
+  }
+  if (CONV) rfma(acc, c, accn);
+  return acc;
 }
 
 template <int SP>
@@ -44,36 +111,51 @@ __device__ __forceinline__ bool is_unknown(int ix, int iy, int n) {
   return (ix | iy) != 0;
 }
 
-template <class T, int SP, bool CONV>
-__device__ __forceinline__ cpx<T> op_apply(const T* tab, int n, int ix, int iy, const cpx<T>* x, cpx<T> a, T b,
-                                           T c) {
-  if (SP == 2) return q2_op<T, CONV>(tab, n, ix, iy, x, a, b, c);
-  return q1_op<T, CONV>(tab, n, ix, iy, x, a, b, c);
-}
-template <class T, int SP, bool CONV>
-__device__ __forceinline__ cpx<T> op_diag(const T* tab, int n, int ix, int iy, cpx<T> a, T b, T c) {
-  if (SP == 2) return q2_diag<T, CONV>(tab, n, ix, iy, a, b, c);
-  return q1_diag<T, CONV>(tab, n, ix, iy, a, b, c);
-}
-
-template <class T, int SP, bool CONV>
-__device__ void sor_colour(const T* tab, int n, cpx<T>* x, const cpx<T>* b, int colour, cpx<T> a, T bb, T c,
-                           T omega) {
-  constexpr int NC = SP == 2 ? 3 : 2;
-  const int cx = colour % NC, cy = colour / NC;
-  int fx, nx, fy, ny;
-  colour_axis<SP>(n, cx, fx, nx);
-  colour_axis<SP>(n, cy, fy, ny);
-  const int tot = nx * ny;
-  for (int q = threadIdx.x; q < tot; q += blockDim.x) {
-    const int ix = fx + NC * (q % nx);
-    const int iy = fy + NC * (q / nx);
-    if (SP == 1 && (ix | iy) == 0) continue;
-    const size_t id = (size_t)iy * n + ix;
-    const cpx<T> ax = op_apply<T, SP, CONV>(tab, n, ix, iy, x, a, bb, c);
-    const cpx<T> dg = op_diag<T, SP, CONV>(tab, n, ix, iy, a, bb, c);
-    const cpx<T> upd = cdiv(b[id] - ax, dg);
-    x[id] = x[id] + omega * upd;
+// One multicolour SOR colour on all fields of the job.  Q2: the colour
+// (ix mod 3, iy mod 3) is walked one node-type subclass (ix mod 2, iy mod 2)
+// at a time, i.e. the residue class mod 6, so that each warp's nodes share
+// one weight set.  Q1: colours (ix mod 2, iy mod 2), pinned corner skipped.
+template <class T, int SP, bool CONV, bool CW>
+__device__ void sor_colour(int n, cpx<T>* const* X, const cpx<T>* const* B, int nf, const cpx<T>* sw,
+                           const cpx<T>* sdi, const T* n2d, T c, int colour, T omega, const T* q1tab = nullptr,
+                           cpx<T> ca = cpx<T>{}, T cb = T(0)) {
+  if (SP == 2) {
+    const int cx = colour % 3, cy = colour / 3;
+    for (int sub = 0; sub < 4; ++sub) {
+      const int px = sub & 1, py = sub >> 1;
+      const int rx = cx + 3 * ((px + cx) & 1), ry = cy + 3 * ((py + cy) & 1);
+      const int fx = rx >= 1 ? rx : 6, fy = ry >= 1 ? ry : 6;
+      const int nx = fx <= n - 2 ? (n - 2 - fx) / 6 + 1 : 0;
+      const int ny = fy <= n - 2 ? (n - 2 - fy) / 6 + 1 : 0;
+      const int cnt = nx * ny;
+      const cpx<T>* w = sw + sub * 25;
+      const cpx<T> di = sdi[sub];
+      for (int q = threadIdx.x; q < nf * cnt; q += blockDim.x) {
+        const int f = q / cnt, r = q - f * cnt;
+        const int ix = fx + 6 * (r % nx), iy = fy + 6 * (r / nx);
+        const size_t id = (size_t)iy * n + ix;
+        cpx<T>* x = X[f];
+        const cpx<T> ax = stencil<T, SP, CONV, CW>(w, CONV ? n2d + id * 25 : nullptr, c, n, ix, iy, x);
+        const cpx<T> res = B[f][id] - ax;
+        x[id] = x[id] + omega * (CW ? res * di : di.x * res);
+      }
+    }
+  } else {
+    const int cx = colour & 1, cy = colour >> 1;
+    const int nx = (n - 1 - cx) / 2 + 1, ny = (n - 1 - cy) / 2 + 1;
+    const int cnt = nx * ny;
+    for (int q = threadIdx.x; q < nf * cnt; q += blockDim.x) {
+      const int f = q / cnt, r = q - f * cnt;
+      const int ix = cx + 2 * (r % nx), iy = cy + 2 * (r / nx);
+      if ((ix | iy) == 0) continue;
+      const size_t id = (size_t)iy * n + ix;
+      cpx<T>* x = X[f];
+      // separable evaluation from the 1-D bands: the pinned Laplacian's
+      // near-constant mode needs exactly zero row sums of K_p
+      const cpx<T> ax = q1_op<T, false>(q1tab, n, ix, iy, x, ca, cb, T(0));
+      const cpx<T> dg = q1_diag<T, false>(q1tab, n, ix, iy, ca, cb, T(0));
+      x[id] = x[id] + omega * cdiv(B[f][id] - ax, dg);
+    }
   }
 }
 
@@ -106,27 +188,39 @@ __device__ __forceinline__ void q2_pw(int f, int& base, float w[3]) {
   }
 }
 
-template <class T, int SP, bool CONV>
-__global__ void __launch_bounds__(MG_THREADS) mg_kernel(MGLaunch<T> L) {
+template <class T, int SP, bool CONV, bool CW>
+__global__ void __launch_bounds__(MG_THREADS, MG_MINB) mg_kernel(MGLaunch<T> L) {
+  __shared__ cpx<T> sw[100];
+  __shared__ cpx<T> sdi[9];
+  __shared__ cpx<T>* Xs[PINT_MAXLEV][PINT_MAXF];
+  __shared__ const cpx<T>* Bs[PINT_MAXLEV][PINT_MAXF];
+  __shared__ cpx<T>* Rs[PINT_MAXLEV][PINT_MAXF];
   const FieldJob jb = L.jobs[blockIdx.x];
   if (L.active && !L.active[jb.freq]) return;
   const OpCoef oc = L.ops[jb.op];
-  const cpx<T> a = mkc<T>(T(oc.ar), T(oc.ai));
-  const T bb = T(oc.b), cc = T(oc.c);
+  const cpx<double> a = mkc<double>(oc.ar, oc.ai);
+  const double bb = oc.b;
+  const T cc = T(oc.c);
+  const cpx<T> ca = mkc<T>(T(oc.ar), T(oc.ai));
+  const T cbT = T(oc.b);
   const T omega = T(L.omega);
-  cpx<T>* ws = L.ws + (size_t)blockIdx.x * L.lay.per_job;
-  cpx<T>* x0 = L.xbase + jb.x_off;
-  const cpx<T>* b0 = L.bbase + jb.b_off;
+  const int nf = jb.nf;
   const int nl = L.lay.nlev;
   const int last = nl - 1;
   const double* inv = L.coarse_inv + (size_t)jb.op * PINT_NC_MAX * PINT_NC_MAX * 2;
-
-  auto Xl = [&](int l) -> cpx<T>* { return l == 0 ? x0 : ws + L.lay.off_x[l]; };
-  auto Bl = [&](int l) -> const cpx<T>* { return l == 0 ? b0 : ws + L.lay.off_b[l]; };
-
+  if (threadIdx.x < PINT_MAXF) {
+    const int f = threadIdx.x;
+    cpx<T>* ws = L.ws + ((size_t)blockIdx.x * L.fields_per_job + (f < nf ? f : 0)) * L.lay.per_job;
+    for (int l = 0; l < nl; ++l) {
+      Xs[l][f] = l == 0 ? L.xbase + jb.x_off[f < nf ? f : 0] : ws + L.lay.off_x[l];
+      Bs[l][f] = l == 0 ? L.bbase + jb.b_off[f < nf ? f : 0] : ws + L.lay.off_b[l];
+      Rs[l][f] = ws + L.lay.off_r[l];
+    }
+  }
+  __syncthreads();
   {
     const int n0 = L.lay.n[0];
-    for (int i = threadIdx.x; i < n0 * n0; i += blockDim.x) x0[i] = czero<T>();
+    for (int q = threadIdx.x; q < nf * n0 * n0; q += blockDim.x) Xs[0][q / (n0 * n0)][q % (n0 * n0)] = czero<T>();
   }
   __syncthreads();
 
@@ -134,28 +228,28 @@ __global__ void __launch_bounds__(MG_THREADS) mg_kernel(MGLaunch<T> L) {
     // ---------------- down sweep
     for (int l = 0; l < last; ++l) {
       const int n = L.lay.n[l];
-      const T* tab = SP == 2 ? L.tabs.q2[l] : L.tabs.q1[l];
-      cpx<T>* X = Xl(l);
-      const cpx<T>* B = Bl(l);
+      const T* n2d = CONV ? L.n2d[l] : nullptr;
+      level_weights<T, SP>(L.t64, l, n, a, bb, sw, sdi);
+      __syncthreads();
       constexpr int NCOL = SP == 2 ? 9 : 4;
       for (int s = 0; s < L.pre; ++s)
         for (int col = 0; col < NCOL; ++col) {
-          sor_colour<T, SP, CONV>(tab, n, X, B, col, a, bb, cc, omega);
+          sor_colour<T, SP, CONV, CW>(n, Xs[l], Bs[l], nf, sw, sdi, n2d, cc, col, omega, L.tabs.q1[l], ca, cbT);
           __syncthreads();
         }
-      cpx<T>* R = ws + L.lay.off_r[l];
-      for (int i = threadIdx.x; i < n * n; i += blockDim.x) {
+      for (int q = threadIdx.x; q < nf * n * n; q += blockDim.x) {
+        const int f = q / (n * n), i = q % (n * n);
         const int ix = i % n, iy = i / n;
         cpx<T> r = czero<T>();
-        if (is_unknown<SP>(ix, iy, n)) r = B[i] - op_apply<T, SP, CONV>(tab, n, ix, iy, X, a, bb, cc);
-        R[i] = r;
+        if (is_unknown<SP>(ix, iy, n)) r = Bs[l][f][i] - q1_op<T, false>(L.tabs.q1[l], n, ix, iy, Xs[l][f], ca, cbT, T(0));
+        Rs[l][f][i] = r;
       }
       __syncthreads();
       const int nc = L.lay.n[l + 1];
-      cpx<T>* Bc = ws + L.lay.off_b[l + 1];
-      cpx<T>* Xc = ws + L.lay.off_x[l + 1];
-      for (int i = threadIdx.x; i < nc * nc; i += blockDim.x) {
+      for (int q = threadIdx.x; q < nf * nc * nc; q += blockDim.x) {
+        const int f = q / (nc * nc), i = q % (nc * nc);
         const int ix = i % nc, iy = i / nc;
+        const cpx<T>* R = Rs[l][f];
         cpx<T> acc = czero<T>();
         if (is_unknown<SP>(ix, iy, nc)) {
           if (SP == 2) {
@@ -168,8 +262,8 @@ __global__ void __launch_bounds__(MG_THREADS) mg_kernel(MGLaunch<T> L) {
 #pragma unroll
               for (int ox = -3; ox <= 3; ++ox) {
                 const T wx = T(q2_rw(ix, ox));
-                const int fx = clampi(2 * ix + ox, 0, n - 1);
-                rfma(s, wx, R[(size_t)fy * n + fx]);
+                if (wx == T(0)) continue;
+                rfma(s, wx, R[(size_t)fy * n + clampi(2 * ix + ox, 0, n - 1)]);
               }
               rfma(acc, wy, s);
             }
@@ -190,19 +284,19 @@ __global__ void __launch_bounds__(MG_THREADS) mg_kernel(MGLaunch<T> L) {
             }
           }
         }
-        Bc[i] = acc;
-        Xc[i] = czero<T>();
+        const_cast<cpx<T>*>(Bs[l + 1][f])[i] = acc;
+        Xs[l + 1][f][i] = czero<T>();
       }
       __syncthreads();
     }
     // ---------------- coarsest level: dense FP64 solve
     {
       const int n = L.lay.n[last];
-      cpx<T>* X = Xl(last);
-      const cpx<T>* B = Bl(last);
-      const int inner = SP == 2 ? n - 2 : n;  // interior nodes per side (Q2) / all (Q1)
+      const int inner = SP == 2 ? n - 2 : n;
       const int nu = SP == 2 ? inner * inner : n * n - 1;
-      for (int u = threadIdx.x; u < nu; u += blockDim.x) {
+      for (int q = threadIdx.x; q < nf * nu; q += blockDim.x) {
+        const int f = q / nu, u = q % nu;
+        const cpx<T>* B = Bs[last][f];
         double sr = 0.0, si = 0.0;
         for (int k = 0; k < nu; ++k) {
           const int node = SP == 2 ? (1 + k / inner) * n + (1 + k % inner) : k + 1;
@@ -212,7 +306,7 @@ __global__ void __launch_bounds__(MG_THREADS) mg_kernel(MGLaunch<T> L) {
           si += ir * (double)bk.y + ii * (double)bk.x;
         }
         const int node = SP == 2 ? (1 + u / inner) * n + (1 + u % inner) : u + 1;
-        X[node] = mkc<T>(T(sr), T(si));
+        Xs[last][f][node] = mkc<T>(T(sr), T(si));
       }
       __syncthreads();
     }
@@ -220,13 +314,13 @@ __global__ void __launch_bounds__(MG_THREADS) mg_kernel(MGLaunch<T> L) {
     for (int l = last - 1; l >= 0; --l) {
       const int n = L.lay.n[l];
       const int nc = L.lay.n[l + 1];
-      const T* tab = SP == 2 ? L.tabs.q2[l] : L.tabs.q1[l];
-      cpx<T>* X = Xl(l);
-      const cpx<T>* B = Bl(l);
-      const cpx<T>* Xc = ws + L.lay.off_x[l + 1];
-      for (int i = threadIdx.x; i < n * n; i += blockDim.x) {
+      const T* n2d = CONV ? L.n2d[l] : nullptr;
+      level_weights<T, SP>(L.t64, l, n, a, bb, sw, sdi);
+      for (int q = threadIdx.x; q < nf * n * n; q += blockDim.x) {
+        const int f = q / (n * n), i = q % (n * n);
         const int ix = i % n, iy = i / n;
         if (!is_unknown<SP>(ix, iy, n)) continue;
+        const cpx<T>* Xc = Xs[l + 1][f];
         cpx<T> acc = czero<T>();
         if (SP == 2) {
           int bx, by;
@@ -255,17 +349,276 @@ __global__ void __launch_bounds__(MG_THREADS) mg_kernel(MGLaunch<T> L) {
           rfma(acc, wy0, s0);
           rfma(acc, wy1, s1);
         }
-        X[i] = X[i] + acc;
+        Xs[l][f][i] = Xs[l][f][i] + acc;
       }
       __syncthreads();
       constexpr int NCOL = SP == 2 ? 9 : 4;
       for (int s = 0; s < L.post; ++s)
         for (int col = NCOL - 1; col >= 0; --col) {
-          sor_colour<T, SP, CONV>(tab, n, X, B, col, a, bb, cc, omega);
+          sor_colour<T, SP, CONV, CW>(n, Xs[l], Bs[l], nf, sw, sdi, n2d, cc, col, omega, L.tabs.q1[l], ca, cbT);
           __syncthreads();
         }
     }
     if (last == 0) break;  // single level: the direct solve is exact
+  }
+}
+
+// ============================================================================
+// Q2 multigrid in a class-blocked layout.
+//
+// Every level of a velocity field is stored as 36 dense sub-grids of equal
+// size W6 x W6 (W6 = ceil(n / 6)), one per residue class (ix mod 6,
+// iy mod 6).  A colour (ix mod 3, iy mod 3) of the multicolour SOR is the
+// union of four classes, which are exactly the four node types
+// (vertex / midpoint in x and y).  A warp working through one class
+// therefore has uniform stencil weights, couplings that are zero for its
+// node type are skipped without divergence, loads coalesce, and every
+// neighbour sits at a fixed offset delta[class][k] from the node (a
+// per-level table in shared memory).  The input field is permuted into this
+// layout at the start of a solve and the result permuted back at the end.
+// ============================================================================
+struct BLay {
+  int w6;        // class width = ceil(n / 6)
+  int s;         // class size w6 * w6
+  unsigned mg;   // ceil(2^32 / w6): q / w6 == umulhi(q, mg) for the q used here
+};
+
+__host__ __device__ __forceinline__ BLay make_blay(int n) {
+  BLay b;
+  b.w6 = (n + 5) / 6;
+  b.s = b.w6 * b.w6;
+  b.mg = (unsigned)((0x100000000ull + b.w6 - 1) / b.w6);
+  return b;
+}
+__device__ __forceinline__ int bidx(const BLay& b, int ix, int iy) {
+  return ((ix % 6) + 6 * (iy % 6)) * b.s + (iy / 6) * b.w6 + ix / 6;
+}
+__device__ __forceinline__ int udiv(unsigned q, unsigned mg) { return (int)__umulhi(q, mg); }
+
+// Neighbour offsets of one level: delta[cls * 25 + (dy + 2) * 5 + (dx + 2)].
+__device__ void level_deltas(const BLay& b, int* delta) {
+  for (int q = threadIdx.x; q < 36 * 25; q += blockDim.x) {
+    const int cls = q / 25, k = q % 25;
+    const int rx = cls % 6, ry = cls / 6, dx = k % 5 - 2, dy = k / 5 - 2;
+    const int ax = rx + dx, ay = ry + dy;
+    const int sx = ax < 0 ? -1 : (ax >= 6 ? 1 : 0), sy = ay < 0 ? -1 : (ay >= 6 ? 1 : 0);
+    const int rxn = ax - 6 * sx, ryn = ay - 6 * sy;
+    delta[q] = ((rxn - rx) + 6 * (ryn - ry)) * b.s + sy * b.w6 + sx;
+  }
+}
+
+// (A x) at the node with blocked index id in class (rx, ry).
+template <class T, bool CONV, bool CW>
+__device__ __forceinline__ cpx<T> stencil_b(const cpx<T>* __restrict__ w, const int* __restrict__ dl,
+                                            const T* __restrict__ nrow, T c, int rx, int ry, int id,
+                                            const cpx<T>* __restrict__ x) {
+  cpx<T> acc = czero<T>(), accn = czero<T>();
+#pragma unroll
+  for (int dy = -2; dy <= 2; ++dy) {
+    if ((ry & 1) && (dy == -2 || dy == 2)) continue;  // midpoint rows couple to +-1 only
+#pragma unroll
+    for (int dx = -2; dx <= 2; ++dx) {
+      if ((rx & 1) && (dx == -2 || dx == 2)) continue;
+      const int k = (dy + 2) * 5 + (dx + 2);
+      const cpx<T> v = x[id + dl[k]];
+      if (CW)
+        acc = acc + w[k] * v;
+      else
+        rfma(acc, w[k].x, v);
+      if (CONV) rfma(accn, nrow[k], v);
+    }
+  }
+  if (CONV) rfma(acc, c, accn);
+  return acc;
+}
+
+template <class T, bool CONV, bool CW>
+__device__ void sor_colour_b(int n, const BLay& b, cpx<T>* X, const cpx<T>* B, const cpx<T>* sw, const cpx<T>* sdi,
+                             const int* sdl, const T* n2d, T c, int colour, T omega) {
+  const int ccx = colour % 3, ccy = colour / 3;
+  const int tot = b.s;
+  for (int sub = 0; sub < 4; ++sub) {
+    const int rx = ccx + 3 * (sub & 1), ry = ccy + 3 * (sub >> 1);
+    const int type = (rx & 1) + 2 * (ry & 1), cls = rx + 6 * ry;
+    const cpx<T>* w = sw + type * 25;
+    const int* dl = sdl + cls * 25;
+    const cpx<T> di = sdi[type];
+    for (int q = threadIdx.x; q < tot; q += blockDim.x) {
+      const int my = udiv(q, b.mg), mx = q - my * b.w6;
+      const int ix = 6 * mx + rx, iy = 6 * my + ry;
+      if (ix < 1 || iy < 1 || ix > n - 2 || iy > n - 2) continue;
+      const int id = cls * b.s + q;
+      const cpx<T> ax = stencil_b<T, CONV, CW>(w, dl, CONV ? n2d + (size_t)id * 25 : nullptr, c, rx, ry, id, X);
+      const cpx<T> res = B[id] - ax;
+      X[id] = X[id] + omega * (CW ? res * di : di.x * res);
+    }
+  }
+}
+
+template <class T, bool CONV, bool CW>
+__global__ void __launch_bounds__(MG_THREADS, MG_MINB) mg_q2b_kernel(MGLaunch<T> L) {
+  __shared__ cpx<T> sw[100];
+  __shared__ cpx<T> sdi[9];
+  __shared__ int sdl[36 * 25];
+  const FieldJob jb = L.jobs[blockIdx.x];
+  if (L.active && !L.active[jb.freq]) return;
+  const OpCoef oc = L.ops[jb.op];
+  const cpx<double> a = mkc<double>(oc.ar, oc.ai);
+  const double bb = oc.b;
+  const T cc = T(oc.c);
+  const T omega = T(L.omega);
+  const int nl = L.lay.nlev;
+  const int last = nl - 1;
+  const double* inv = L.coarse_inv + (size_t)jb.op * PINT_NC_MAX * PINT_NC_MAX * 2;
+  cpx<T>* ws = L.ws + (size_t)blockIdx.x * L.fields_per_job * L.lay.per_job;
+  auto Xl = [&](int l) { return ws + L.lay.off_x[l]; };
+  auto Bl = [&](int l) { return ws + L.lay.off_b[l]; };
+  auto Rl = [&](int l) { return ws + L.lay.off_r[l]; };
+  const int n0 = L.lay.n[0];
+  const BLay b0 = make_blay(n0);
+  // permute the right-hand side into the blocked layout; zero the iterate
+  // (padding slots of the blocked arrays are zeroed once here and never written)
+  {
+    cpx<T>* B0 = Bl(0);
+    cpx<T>* X0 = Xl(0);
+    for (int q = threadIdx.x; q < 36 * b0.s; q += blockDim.x) {
+      B0[q] = czero<T>();
+      X0[q] = czero<T>();
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n0 * n0; i += blockDim.x) {
+      const int ix = i % n0, iy = i / n0;
+      if (is_unknown<2>(ix, iy, n0)) B0[bidx(b0, ix, iy)] = L.bbase[jb.b_off[0] + i];
+    }
+  }
+  __syncthreads();
+
+  for (int cyc = 0; cyc < L.cycles; ++cyc) {
+    for (int l = 0; l < last; ++l) {
+      const int n = L.lay.n[l];
+      const BLay b = make_blay(n);
+      const T* n2d = CONV ? L.n2d[l] : nullptr;
+      cpx<T>* X = Xl(l);
+      const cpx<T>* B = Bl(l);
+      level_weights<T, 2>(L.t64, l, n, a, bb, sw, sdi);
+      level_deltas(b, sdl);
+      __syncthreads();
+      for (int s = 0; s < L.pre; ++s)
+        for (int col = 0; col < 9; ++col) {
+          sor_colour_b<T, CONV, CW>(n, b, X, B, sw, sdi, sdl, n2d, cc, col, omega);
+          __syncthreads();
+        }
+      // residual over all classes (non-unknown and padding slots get 0)
+      cpx<T>* R = Rl(l);
+      for (int q = threadIdx.x; q < 36 * b.s; q += blockDim.x) {
+        const int cls = q / b.s, i = q - cls * b.s;
+        const int rx = cls % 6, ry = cls / 6;
+        const int my = udiv(i, b.mg), mx = i - my * b.w6;
+        const int ix = 6 * mx + rx, iy = 6 * my + ry;
+        cpx<T> r = czero<T>();
+        if (ix >= 1 && iy >= 1 && ix <= n - 2 && iy <= n - 2)
+          r = B[q] - stencil_b<T, CONV, CW>(sw + ((rx & 1) + 2 * (ry & 1)) * 25, sdl + cls * 25,
+                                            CONV ? n2d + (size_t)q * 25 : nullptr, cc, rx, ry, q, X);
+        R[q] = r;
+      }
+      __syncthreads();
+      // restriction R = P^T onto the coarse level, coarse iterate zeroed
+      const int nc = L.lay.n[l + 1];
+      const BLay bc = make_blay(nc);
+      cpx<T>* Bc = Bl(l + 1);
+      cpx<T>* Xc = Xl(l + 1);
+      for (int q = threadIdx.x; q < 36 * bc.s; q += blockDim.x) {
+        const int cls = q / bc.s, i = q - cls * bc.s;
+        const int rx = cls % 6, ry = cls / 6;
+        const int my = udiv(i, bc.mg), mx = i - my * bc.w6;
+        const int ix = 6 * mx + rx, iy = 6 * my + ry;
+        cpx<T> acc = czero<T>();
+        if (ix >= 1 && iy >= 1 && ix <= nc - 2 && iy <= nc - 2) {
+#pragma unroll
+          for (int oy = -3; oy <= 3; ++oy) {
+            const T wy = T(q2_rw(iy, oy));
+            if (wy == T(0)) continue;
+#pragma unroll
+            for (int ox = -3; ox <= 3; ++ox) {
+              const T wx = T(q2_rw(ix, ox));
+              if (wx == T(0)) continue;
+              rfma(acc, wx * wy, R[bidx(b, 2 * ix + ox, 2 * iy + oy)]);
+            }
+          }
+        }
+        Bc[q] = acc;
+        Xc[q] = czero<T>();
+      }
+      __syncthreads();
+    }
+    // coarsest level: dense FP64 solve
+    {
+      const int n = L.lay.n[last];
+      const BLay b = make_blay(n);
+      const int inner = n - 2, nu = inner * inner;
+      const cpx<T>* Bc = Bl(last);
+      cpx<T>* Xc = Xl(last);
+      for (int u = threadIdx.x; u < nu; u += blockDim.x) {
+        double sr = 0.0, si = 0.0;
+        for (int k = 0; k < nu; ++k) {
+          const cpx<T> bk = Bc[bidx(b, 1 + k % inner, 1 + k / inner)];
+          const double ir = inv[(u * PINT_NC_MAX + k) * 2], ii = inv[(u * PINT_NC_MAX + k) * 2 + 1];
+          sr += ir * (double)bk.x - ii * (double)bk.y;
+          si += ir * (double)bk.y + ii * (double)bk.x;
+        }
+        Xc[bidx(b, 1 + u % inner, 1 + u / inner)] = mkc<T>(T(sr), T(si));
+      }
+      __syncthreads();
+    }
+    for (int l = last - 1; l >= 0; --l) {
+      const int n = L.lay.n[l];
+      const BLay b = make_blay(n);
+      const BLay bc = make_blay(L.lay.n[l + 1]);
+      const T* n2d = CONV ? L.n2d[l] : nullptr;
+      cpx<T>* X = Xl(l);
+      const cpx<T>* B = Bl(l);
+      const cpx<T>* Xc = Xl(l + 1);
+      level_weights<T, 2>(L.t64, l, n, a, bb, sw, sdi);
+      level_deltas(b, sdl);
+      // prolongation onto the fine level
+      for (int q = threadIdx.x; q < 36 * b.s; q += blockDim.x) {
+        const int cls = q / b.s, i = q - cls * b.s;
+        const int rx = cls % 6, ry = cls / 6;
+        const int my = udiv(i, b.mg), mx = i - my * b.w6;
+        const int ix = 6 * mx + rx, iy = 6 * my + ry;
+        if (ix < 1 || iy < 1 || ix > n - 2 || iy > n - 2) continue;
+        int bx, by;
+        float wx[3], wy[3];
+        q2_pw(ix, bx, wx);
+        q2_pw(iy, by, wy);
+        cpx<T> acc = czero<T>();
+#pragma unroll
+        for (int ty = 0; ty < 3; ++ty) {
+          if (wy[ty] == 0.f) continue;
+#pragma unroll
+          for (int tx = 0; tx < 3; ++tx) {
+            if (wx[tx] == 0.f) continue;
+            rfma(acc, T(wx[tx] * wy[ty]), Xc[bidx(bc, bx + tx, by + ty)]);
+          }
+        }
+        X[q] = X[q] + acc;
+      }
+      __syncthreads();
+      for (int s = 0; s < L.post; ++s)
+        for (int col = 8; col >= 0; --col) {
+          sor_colour_b<T, CONV, CW>(n, b, X, B, sw, sdi, sdl, n2d, cc, col, omega);
+          __syncthreads();
+        }
+    }
+    if (last == 0) break;
+  }
+  // permute the result back to the natural layout
+  {
+    const cpx<T>* X0 = Xl(0);
+    for (int i = threadIdx.x; i < n0 * n0; i += blockDim.x) {
+      const int ix = i % n0, iy = i / n0;
+      L.xbase[jb.x_off[0] + i] = is_unknown<2>(ix, iy, n0) ? X0[bidx(b0, ix, iy)] : czero<T>();
+    }
   }
 }
 
@@ -274,72 +627,86 @@ void launch_mg(const MGLaunch<T>& L, cudaStream_t st) {
   if (L.njobs <= 0) return;
   dim3 grid(L.njobs), block(MG_THREADS);
   if (L.space == 2) {
+    // one velocity field per CTA, class-blocked layout in the workspace
     if (L.conv)
-      mg_kernel<T, 2, true><<<grid, block, 0, st>>>(L);
+      mg_q2b_kernel<T, true, true><<<grid, block, 0, st>>>(L);
+    else if (L.cw)
+      mg_q2b_kernel<T, false, true><<<grid, block, 0, st>>>(L);
     else
-      mg_kernel<T, 2, false><<<grid, block, 0, st>>>(L);
+      mg_q2b_kernel<T, false, false><<<grid, block, 0, st>>>(L);
   } else {
-    if (L.conv)
-      mg_kernel<T, 1, true><<<grid, block, 0, st>>>(L);
-    else
-      mg_kernel<T, 1, false><<<grid, block, 0, st>>>(L);
+    mg_kernel<T, 1, false, false><<<grid, block, 0, st>>>(L);
   }
 }
 
 // ---------------------------------------------------------------------------
-// Jacobi-Chebyshev semi-iteration on the mass matrix (finest level).
-// Recurrence (three-term Chebyshev acceleration of the Jacobi iteration with
-// D = diag(M), eigenvalues of D^{-1} M in [lmin, lmax]): x0 = 0, r0 = b,
-// d0 = D^{-1} r0 / theta; x_{k+1} = x_k + d_k; r_{k+1} = r_k - M d_k;
-// rho_{k+1} = 1 / (2 sigma - rho_k); d_{k+1} = rho_{k+1} rho_k d_k +
-// (2 rho_{k+1} / delta) D^{-1} r_{k+1}; theta, delta = (lmax +- lmin) / 2,
-// sigma = theta / delta, rho_0 = 1 / sigma.  `steps` updates of x.
+// Jacobi-Chebyshev semi-iteration on the mass matrix (finest level), for all
+// fields of a job.  Recurrence (three-term Chebyshev acceleration of the
+// Jacobi iteration with D = diag(M), eigenvalues of D^{-1} M in
+// [lmin, lmax]): x0 = 0, r0 = b, d0 = D^{-1} r0 / theta; x_{k+1} = x_k + d_k;
+// r_{k+1} = r_k - M d_k; rho_{k+1} = 1 / (2 sigma - rho_k);
+// d_{k+1} = rho_{k+1} rho_k d_k + (2 rho_{k+1} / delta) D^{-1} r_{k+1};
+// theta, delta = (lmax +- lmin) / 2, sigma = theta / delta, rho_0 = 1 / sigma.
+// `steps` updates of x.
 // ---------------------------------------------------------------------------
 template <class T, int SP>
-__global__ void __launch_bounds__(MG_THREADS) cheb_kernel(ChebLaunch<T> L) {
+__global__ void __launch_bounds__(MG_THREADS, MG_MINB) cheb_kernel(ChebLaunch<T> L) {
+  __shared__ cpx<T> sw[100];
+  __shared__ cpx<T> sdi[9];
   const FieldJob jb = L.jobs[blockIdx.x];
   if (L.active && !L.active[jb.freq]) return;
+  const int nf = jb.nf;
   const int n = SP == 2 ? 2 * L.tabs.N[0] + 1 : L.tabs.N[0] + 1;
-  const T* tab = SP == 2 ? L.tabs.q2[0] : L.tabs.q1[0];
-  cpx<T>* x = L.xbase + jb.x_off;
-  const cpx<T>* b = L.bbase + jb.b_off;
-  cpx<T>* r = L.ws + (size_t)blockIdx.x * L.per_job;
-  cpx<T>* d = r + (size_t)n * n;
+  const int nn = n * n;
+  level_weights<T, SP>(L.t64, 0, n, mkc<double>(1.0, 0.0), 0.0, sw, sdi);
   const double theta = 0.5 * (L.lmax + L.lmin), delta = 0.5 * (L.lmax - L.lmin);
   const double sigma = theta / delta;
   double rho = 1.0 / sigma;
-  const cpx<T> one = mkc<T>(T(1), T(0));
-  for (int i = threadIdx.x; i < n * n; i += blockDim.x) {
+  auto X = [&](int f) { return L.xbase + jb.x_off[f]; };
+  auto B = [&](int f) { return L.bbase + jb.b_off[f]; };
+  auto Rr = [&](int f) { return L.ws + ((size_t)blockIdx.x * L.fields_per_job + f) * L.per_job; };
+  __syncthreads();
+  for (int q = threadIdx.x; q < nf * nn; q += blockDim.x) {
+    const int f = q / nn, i = q % nn;
     const int ix = i % n, iy = i / n;
     cpx<T> ri = czero<T>(), di = czero<T>();
     if (is_unknown<SP>(ix, iy, n)) {
-      const T dg = op_diag<T, SP, false>(tab, n, ix, iy, one, T(0), T(0)).x;
-      ri = b[i];
-      di = (T(1) / (dg * T(theta))) * ri;
+      const T dinv = sdi[node_type<SP>(ix, iy, n)].x;
+      ri = B(f)[i];
+      di = (dinv / T(theta)) * ri;
     }
-    r[i] = ri;
-    d[i] = di;
-    x[i] = czero<T>();
+    Rr(f)[i] = ri;
+    Rr(f)[nn + i] = di;
+    X(f)[i] = czero<T>();
   }
   __syncthreads();
   for (int k = 0; k < L.steps; ++k) {
     const bool lastk = (k == L.steps - 1);
-    for (int i = threadIdx.x; i < n * n; i += blockDim.x) {
+    for (int q = threadIdx.x; q < nf * nn; q += blockDim.x) {
+      const int f = q / nn, i = q % nn;
       const int ix = i % n, iy = i / n;
       if (!is_unknown<SP>(ix, iy, n)) continue;
-      x[i] = x[i] + d[i];
-      if (!lastk) r[i] = r[i] - op_apply<T, SP, false>(tab, n, ix, iy, d, one, T(0), T(0));
+      cpx<T>* r = Rr(f);
+      const cpx<T>* d = r + nn;
+      X(f)[i] = X(f)[i] + d[i];
+      if (!lastk) {
+        const int type = node_type<SP>(ix, iy, n);
+        r[i] = r[i] - stencil<T, SP, false, false>(sw + type * (SP == 2 ? 25 : 9), nullptr, T(0), n, ix, iy, d);
+      }
     }
     if (lastk) break;
     __syncthreads();
     const double rho_new = 1.0 / (2.0 * sigma - rho);
     const T c1 = T(rho_new * rho), c2 = T(2.0 * rho_new / delta);
-    for (int i = threadIdx.x; i < n * n; i += blockDim.x) {
+    for (int q = threadIdx.x; q < nf * nn; q += blockDim.x) {
+      const int f = q / nn, i = q % nn;
       const int ix = i % n, iy = i / n;
       if (!is_unknown<SP>(ix, iy, n)) continue;
-      const T dg = op_diag<T, SP, false>(tab, n, ix, iy, one, T(0), T(0)).x;
+      cpx<T>* r = Rr(f);
+      cpx<T>* d = r + nn;
+      const T dinv = sdi[node_type<SP>(ix, iy, n)].x;
       cpx<T> dn = c1 * d[i];
-      rfma(dn, c2 / dg, r[i]);
+      rfma(dn, c2 * dinv, r[i]);
       d[i] = dn;
     }
     rho = rho_new;
@@ -354,6 +721,32 @@ void launch_cheb(const ChebLaunch<T>& L, cudaStream_t st) {
     cheb_kernel<T, 2><<<L.njobs, MG_THREADS, 0, st>>>(L);
   else
     cheb_kernel<T, 1><<<L.njobs, MG_THREADS, 0, st>>>(L);
+}
+
+// ---------------------------------------------------------------------------
+// Per-node convection stencil tables (FP64 -> T), one level.
+// ---------------------------------------------------------------------------
+template <class T>
+__global__ void build_n2d_kernel(Tabs<double> t64, int l, T* out) {
+  const int n = 2 * t64.N[l] + 1;
+  const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= (long long)n * n * 25) return;
+  const int k = (int)(q % 25);
+  const long long node = q / 25;
+  const int ix = (int)(node % n), iy = (int)(node / n);
+  const int dx = k % 5, dy = k / 5;
+  const double* tab = t64.q2[l];
+  const double wx = tab[(size_t)(2 * n + ix) * 5 + dx], xx = tab[(size_t)(3 * n + ix) * 5 + dx];
+  const double wy = tab[(size_t)(2 * n + iy) * 5 + dy], xy = tab[(size_t)(3 * n + iy) * 5 + dy];
+  const BLay b = make_blay(n);
+  out[(size_t)bidx(b, ix, iy) * 25 + k] = T(2.0 * (wx * xy - xx * wy));
+}
+
+template <class T>
+void launch_build_n2d(const Tabs<double>& t64, int l, T* out, cudaStream_t st) {
+  const int n = 2 * t64.N[l] + 1;
+  const long long tot = (long long)n * n * 25;
+  build_n2d_kernel<T><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(t64, l, out);
 }
 
 // ---------------------------------------------------------------------------
@@ -449,6 +842,8 @@ void launch_coarse_setup(const Tabs<double>& tabs, const OpCoef* ops, const int*
   coarse_setup_kernel<<<(nops + 63) / 64, 64, 0, st>>>(tabs, ops, op_space, op_conv, nops, inv, status);
 }
 
+template void launch_build_n2d<float>(const Tabs<double>&, int, float*, cudaStream_t);
+template void launch_build_n2d<double>(const Tabs<double>&, int, double*, cudaStream_t);
 template void launch_mg<float>(const MGLaunch<float>&, cudaStream_t);
 template void launch_mg<double>(const MGLaunch<double>&, cudaStream_t);
 template void launch_cheb<float>(const ChebLaunch<float>&, cudaStream_t);

@@ -7,13 +7,17 @@
 
 namespace pint {
 
-// One multigrid / Chebyshev job: a scalar field of one frequency.
-// Offsets are in complex elements, relative to the base pointers of the launch.
+// One multigrid / Chebyshev job: up to PINT_MAXF scalar fields of one
+// frequency that share one operator.  Offsets are in complex elements,
+// relative to the base pointers of the launch.
+#define PINT_MAXF 4
 struct FieldJob {
-  long long x_off;
-  long long b_off;
+  long long x_off[PINT_MAXF];
+  long long b_off[PINT_MAXF];
+  int nf;
   int op;
   int freq;
+  int pad;
 };
 
 // Per-level workspace offsets (complex elements) inside one job's workspace.
@@ -29,6 +33,10 @@ struct MGLayout {
 template <class T>
 struct MGLaunch {
   Tabs<T> tabs;
+  Tabs<double> t64;          // FP64 bands: stencil weights are formed in FP64
+  const T* n2d[PINT_MAXLEV]; // Q2 convection stencil per blocked node [n^2][25] (conv only)
+  int fields_per_job;        // workspace slots per job
+  bool cw;                   // complex operator coefficient (Oseen shifts)
   MGLayout lay;
   const OpCoef* ops;
   const double* coarse_inv;  // complex FP64, [op][PINT_NC_MAX^2][2]
@@ -52,12 +60,14 @@ void launch_mg(const MGLaunch<T>& L, cudaStream_t st);
 template <class T>
 struct ChebLaunch {
   Tabs<T> tabs;
+  Tabs<double> t64;
   const FieldJob* jobs;
   int njobs;
   cpx<T>* xbase;
   const cpx<T>* bbase;
-  cpx<T>* ws;         // 2 fields per job
-  long long per_job;  // complex elements per job
+  cpx<T>* ws;         // 2 fields (r, d) per job field
+  long long per_job;  // complex elements per job field
+  int fields_per_job;
   const int* active;
   int steps;
   double lmin, lmax;
@@ -66,6 +76,12 @@ struct ChebLaunch {
 
 template <class T>
 void launch_cheb(const ChebLaunch<T>& L, cudaStream_t st);
+
+// Per-node Q2 convection stencil N = 2 (W1 (x) X1 - X1 (x) W1), formed in
+// FP64 and rounded once: out[b(ix, iy) * 25 + dy * 5 + dx] at level l, with
+// b the class-blocked node index of the multigrid layout.
+template <class T>
+void launch_build_n2d(const Tabs<double>& t64, int l, T* out, cudaStream_t st);
 
 // Coarse-grid inverses: for each op, the dense inverse of the operator on
 // the coarsest grid (FP64, Gauss-Jordan with partial pivoting).
