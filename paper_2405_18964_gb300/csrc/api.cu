@@ -428,14 +428,18 @@ void Engine<T>::inner_solve(const cpx<T>* S, cpx<T>* X, int* its_host) {
     cpx<T>* Vn = V + (size_t)(i + 1) * vs;
     block_prec(Vi, Zi, G.active);
     block_matvec(c->d_blkZ, Zi, Vn, G.active);
-    PROF(c, PINT_PROF_INNER, 3 * (i + 1) + 4);
-    for (int l = 0; l <= i; ++l) {
-      double* h = G.H + ((size_t)l * m + i) * 2;
-      launch_bdot<T>(J, nb, V + (size_t)l * vs, Vn, nb, nb, G.partial, h, hs, G.active, false, st);
-      launch_baxpy_dev<T>(J, nb, V + (size_t)l * vs, Vn, nb, h, hs, 1.0, G.active, st);
-    }
+    // classical Gram-Schmidt with one reorthogonalisation (CGS2) against
+    // V_0..V_i for all active frequencies, then the norm of the result
+    const int cnt = i + 1;
+    const int nk = 2 * ((cnt + 7) / 8 + 1) + 2 * 1 + 1 + 1 + 1 + 1;
+    PROF(c, PINT_PROF_INNER, nk + 1);
+    launch_bmdot<T>(J, nb, V, (long long)vs, cnt, Vn, G.cpart, G.H, hs, m, i, false, G.active, st);
+    launch_hcol_gather(J, cnt, G.H, hs, m, i, G.hc, G.active, st);
+    launch_bmaxpy<T>(J, nb, V, (long long)vs, cnt, Vn, G.hc, 256, nullptr, nullptr, 0, G.active, st);
+    launch_bmdot<T>(J, nb, V, (long long)vs, cnt, Vn, G.cpart, G.hc2, 256, 1, 0, false, G.active, st);
     double* hn = G.H + ((size_t)(i + 1) * m + i) * 2;
-    launch_bdot<T>(J, nb, Vn, Vn, nb, nb, G.partial, hn, hs, G.active, true, st);
+    launch_bmaxpy<T>(J, nb, V, (long long)vs, cnt, Vn, G.hc2, 256, G.npart, hn, hs, G.active, st);
+    launch_hcol_add(J, cnt, G.H, hs, m, i, G.hc2, G.active, st);
     launch_bscale_inv<T>(J, nb, Vn, Vn, nb, hn, hs, G.active, st);
     launch_gmres_givens(G, i, c->p.inner_tol, c->p.fixed_inner_its, st);
     cudaMemcpyAsync(c->h_count, G.count, sizeof(int), cudaMemcpyDeviceToHost, st);
@@ -500,8 +504,8 @@ bool valid_params(const pint_params* p, std::string& why) {
   if (p->outer_restart < 1 || p->outer_restart > 200) return why = "outer_restart must be in [1, 200]", false;
   if (p->outer_maxit < 1) return why = "outer_maxit must be positive", false;
   if (!(p->outer_tol > 0)) return why = "outer_tol must be positive", false;
-  if (p->inner_maxit < 1 || p->inner_maxit > 1000) return why = "inner_maxit must be in [1, 1000]", false;
-  if (p->fixed_inner_its < 0 || p->fixed_inner_its > 1000) return why = "fixed_inner_its out of range", false;
+  if (p->inner_maxit < 1 || p->inner_maxit > 127) return why = "inner_maxit must be in [1, 127]", false;
+  if (p->fixed_inner_its < 0 || p->fixed_inner_its > 127) return why = "fixed_inner_its must be in [0, 127]", false;
   if (!(p->inner_tol >= 0)) return why = "inner_tol must be >= 0", false;
   if (p->mg_cycles < 1 || p->mg_pre < 0 || p->mg_post < 0 || p->cheb_steps < 1 || p->uzawa_steps < 1)
     return why = "multigrid / Chebyshev / Uzawa counts must be positive", false;
@@ -790,7 +794,10 @@ pint_status build(pint_ctx* c) {
          c->alloc(&G.cs, sizeof(double) * J * m) && c->alloc(&G.sn, sizeof(double) * 2 * J * m) &&
          c->alloc(&G.beta0, sizeof(double) * J) && c->alloc(&G.y, sizeof(double) * 2 * J * m) &&
          c->alloc(&G.partial, sizeof(double) * 2 * J * GM_CH) && c->alloc(&G.active, sizeof(int) * J) &&
-         c->alloc(&G.its, sizeof(int) * J) && c->alloc(&G.count, sizeof(int));
+         c->alloc(&G.its, sizeof(int) * J) && c->alloc(&G.count, sizeof(int)) &&
+         c->alloc(&G.hc, sizeof(double) * 2 * 128 * J) && c->alloc(&G.hc2, sizeof(double) * 2 * 128 * J) &&
+         c->alloc(&G.npart, sizeof(double) * GM_CH * J) &&
+         c->alloc(&G.cpart, sizeof(double) * 2 * GM_CH * J * (m + 1));
     if (!ok) return c->fail(PINT_ERR_OOM, "device allocation failed (inner GMRES)");
   }
   if (c->fp32)

@@ -230,6 +230,133 @@ __global__ void gmres_combine_kernel(GmresState S, long long n, const cpx<T>* Z,
   x[(size_t)j * n + i] = mkc<T>(T(re), T(im));
 }
 
+// ---- classical Gram-Schmidt over the batched basis ---------------------------
+constexpr int GB = 8;  // basis vectors per pass of the dot kernel
+
+template <class T>
+__global__ void __launch_bounds__(RT) bmdot_partial(int J, long long n, const cpx<T>* V, long long vstride, int l0,
+                                                    int cnt, const cpx<T>* w, double* partial, const int* active) {
+  __shared__ double sh[32];
+  const int j = blockIdx.y, ch = blockIdx.x;
+  if (active && !active[j]) return;
+  const long long per = (n + GM_CH - 1) / GM_CH;
+  const long long lo = ch * per, hi = min(n, lo + per);
+  const cpx<T>* wj = w + (size_t)j * n;
+  // per-thread partial sums in T over a few elements, reduced in FP64
+  T re[GB], im[GB];
+#pragma unroll
+  for (int q = 0; q < GB; ++q) re[q] = im[q] = T(0);
+  for (long long e = lo + threadIdx.x; e < hi; e += blockDim.x) {
+    const cpx<T> v = wj[e];
+#pragma unroll
+    for (int q = 0; q < GB; ++q)
+      if (l0 + q < cnt) {
+        const cpx<T> u = V[(size_t)(l0 + q) * vstride + (size_t)j * n + e];
+        re[q] = fma(u.x, v.x, fma(u.y, v.y, re[q]));  // conj(u) v
+        im[q] = fma(u.x, v.y, fma(-u.y, v.x, im[q]));
+      }
+  }
+  for (int q = 0; q < GB && l0 + q < cnt; ++q) {
+    const double a = block_sum((double)re[q], sh);
+    const double b = block_sum((double)im[q], sh);
+    if (threadIdx.x == 0) {
+      double* p = partial + (((size_t)j * GM_CH + ch) * cnt + (l0 + q)) * 2;
+      p[0] = a;
+      p[1] = b;
+    }
+  }
+}
+
+__global__ void bmdot_reduce(int J, int cnt, const double* partial, double* H, long long hs, int m, int col,
+                             bool add, const int* active) {
+  const int j = blockIdx.y;
+  const int l = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (l >= cnt) return;
+  if (active && !active[j]) return;
+  double re = 0, im = 0;
+  for (int c = lane; c < GM_CH; c += 32) {
+    re += partial[(((size_t)j * GM_CH + c) * cnt + l) * 2];
+    im += partial[(((size_t)j * GM_CH + c) * cnt + l) * 2 + 1];
+  }
+  re = warp_sum(re);
+  im = warp_sum(im);
+  if (lane == 0) {
+    double* h = H + (size_t)j * hs + ((size_t)l * m + col) * 2;
+    if (add) {
+      h[0] += re;
+      h[1] += im;
+    } else {
+      h[0] = re;
+      h[1] = im;
+    }
+  }
+}
+
+// coefficients of the current pass are the last written ones: for the first
+// pass H itself, for the second pass the increment is passed separately
+template <class T>
+__global__ void __launch_bounds__(RT) bmaxpy_kernel(int J, long long n, const cpx<T>* V, long long vstride,
+                                                    int cnt, cpx<T>* w, const double* coef, long long cs_j,
+                                                    double* nrm_partial, const int* active) {
+  __shared__ double sh[32];
+  __shared__ cpx<T> hc[128];
+  const int j = blockIdx.y, ch = blockIdx.x;
+  if (active && !active[j]) return;
+  for (int l = threadIdx.x; l < cnt; l += blockDim.x)
+    hc[l] = mkc<T>(T(coef[(size_t)j * cs_j + 2 * l]), T(coef[(size_t)j * cs_j + 2 * l + 1]));
+  __syncthreads();
+  const long long per = (n + GM_CH - 1) / GM_CH;
+  const long long lo = ch * per, hi = min(n, lo + per);
+  cpx<T>* wj = w + (size_t)j * n;
+  T nr = T(0);
+  for (long long e = lo + threadIdx.x; e < hi; e += blockDim.x) {
+    cpx<T> acc = wj[e];
+    for (int l = 0; l < cnt; ++l) acc = acc - hc[l] * V[(size_t)l * vstride + (size_t)j * n + e];
+    wj[e] = acc;
+    nr = fma(acc.x, acc.x, fma(acc.y, acc.y, nr));
+  }
+  if (nrm_partial) {
+    const double t = block_sum((double)nr, sh);
+    if (threadIdx.x == 0) nrm_partial[(size_t)j * GM_CH + ch] = t;
+  }
+}
+
+// copy one H column (rows 0..cnt-1) into a contiguous coefficient buffer
+__global__ void hcol_gather(int J, int cnt, const double* H, long long hs, int m, int col, double* out,
+                            const int* active) {
+  const int j = blockIdx.x;
+  if (active && !active[j]) return;
+  for (int l = threadIdx.x; l < cnt; l += blockDim.x) {
+    out[((size_t)j * 128 + l) * 2] = H[(size_t)j * hs + ((size_t)l * m + col) * 2];
+    out[((size_t)j * 128 + l) * 2 + 1] = H[(size_t)j * hs + ((size_t)l * m + col) * 2 + 1];
+  }
+}
+
+__global__ void hcol_add(int J, int cnt, double* H, long long hs, int m, int col, const double* inc,
+                         const int* active) {
+  const int j = blockIdx.x;
+  if (active && !active[j]) return;
+  for (int l = threadIdx.x; l < cnt; l += blockDim.x) {
+    H[(size_t)j * hs + ((size_t)l * m + col) * 2] += inc[((size_t)j * 128 + l) * 2];
+    H[(size_t)j * hs + ((size_t)l * m + col) * 2 + 1] += inc[((size_t)j * 128 + l) * 2 + 1];
+  }
+}
+
+__global__ void nrm_reduce(int J, const double* nrm_partial, double* nrm, long long ns, const int* active) {
+  const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (j >= J) return;
+  if (active && !active[j]) return;
+  double s = 0;
+  for (int c = lane; c < GM_CH; c += 32) s += nrm_partial[(size_t)j * GM_CH + c];
+  s = warp_sum(s);
+  if (lane == 0) {
+    nrm[(size_t)j * ns] = sqrt(s > 0.0 ? s : 0.0);
+    nrm[(size_t)j * ns + 1] = 0.0;
+  }
+}
+
 // ---- outer ------------------------------------------------------------------
 constexpr int MB = 8;  // vectors per multi-dot pass
 
@@ -321,6 +448,33 @@ void launch_gmres_finish(GmresState& S, long long n, const cpx<T>* Z, long long 
   gmres_combine_kernel<T><<<dim3(nb(n, RT), S.J), RT, 0, st>>>(S, n, Z, zstride_l, x);
 }
 
+template <class T>
+void launch_bmdot(int J, long long n, const cpx<T>* V, long long vstride, int cnt, const cpx<T>* w,
+                  double* partial, double* H, long long hs, int m, int col, bool add, const int* active,
+                  cudaStream_t st) {
+  for (int l0 = 0; l0 < cnt; l0 += GB)
+    bmdot_partial<T><<<dim3(GM_CH, J), RT, 0, st>>>(J, n, V, vstride, l0, cnt, w, partial, active);
+  bmdot_reduce<<<dim3((cnt + 7) / 8, J), 256, 0, st>>>(J, cnt, partial, H, hs, m, col, add, active);
+}
+
+template <class T>
+void launch_bmaxpy(int J, long long n, const cpx<T>* V, long long vstride, int cnt, cpx<T>* w,
+                   const double* coef, long long cs_j, double* nrm_partial, double* nrm, long long ns,
+                   const int* active, cudaStream_t st) {
+  bmaxpy_kernel<T><<<dim3(GM_CH, J), RT, 0, st>>>(J, n, V, vstride, cnt, w, coef, cs_j, nrm_partial, active);
+  if (nrm_partial) nrm_reduce<<<nb(J, 8), 256, 0, st>>>(J, nrm_partial, nrm, ns, active);
+}
+
+void launch_hcol_gather(int J, int cnt, const double* H, long long hs, int m, int col, double* out,
+                        const int* active, cudaStream_t st) {
+  hcol_gather<<<J, 128, 0, st>>>(J, cnt, H, hs, m, col, out, active);
+}
+
+void launch_hcol_add(int J, int cnt, double* H, long long hs, int m, int col, const double* inc,
+                     const int* active, cudaStream_t st) {
+  hcol_add<<<J, 128, 0, st>>>(J, cnt, H, hs, m, col, inc, active);
+}
+
 void launch_mdot(const double* V, int cnt, const double* w, long long n, double* partial, double* h,
                  cudaStream_t st) {
   for (int l0 = 0; l0 < cnt; l0 += MB) {
@@ -350,7 +504,11 @@ void launch_scale_inv_dev(const double* x, const double* s, double* y, long long
   template void launch_bscale_inv<T>(int, long long, const cpx<T>*, cpx<T>*, long long, const double*,      \
                                      long long, const int*, cudaStream_t);                                  \
   template void launch_gmres_finish<T>(GmresState&, long long, const cpx<T>*, long long, cpx<T>*,           \
-                                       cudaStream_t);
+                                       cudaStream_t);                                                       \
+  template void launch_bmdot<T>(int, long long, const cpx<T>*, long long, int, const cpx<T>*, double*,      \
+                                double*, long long, int, int, bool, const int*, cudaStream_t);               \
+  template void launch_bmaxpy<T>(int, long long, const cpx<T>*, long long, int, cpx<T>*, const double*,     \
+                                 long long, double*, double*, long long, const int*, cudaStream_t);
 PINT_INST(float)
 PINT_INST(double)
 #undef PINT_INST

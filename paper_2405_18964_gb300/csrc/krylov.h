@@ -17,6 +17,10 @@ struct GmresState {
   int* active;        // [J]
   int* its;           // [J]
   int* count;         // [1]
+  double* hc;         // [J][128] complex: gathered Gram-Schmidt coefficients
+  double* hc2;        // [J][128] complex: second-pass increments
+  double* npart;      // [J][GM_CH] norm partial sums
+  double* cpart;      // [J][GM_CH][m+1] complex dot partials
 };
 constexpr int GM_CH = 32;  // reduction chunks per frequency
 
@@ -44,6 +48,32 @@ void launch_gmres_givens(GmresState& S, int i, double tol, int fixed, cudaStream
 template <class T>
 void launch_gmres_finish(GmresState& S, long long n, const cpx<T>* Z, long long zstride_l, cpx<T>* x,
                          cudaStream_t st);
+
+// Classical Gram-Schmidt step for all active frequencies against the basis
+// V_0..V_cnt-1 (V_l = V + l * vstride, frequency j at + j * n):
+//   add = false: H[j][l][col] = <V_l, w>      add = true: H[j][l][col] += <V_l, w>
+// (H complex FP64 with per-frequency stride hs and row stride m).
+// partial: [J][GM_CH][cnt] complex scratch.
+template <class T>
+void launch_bmdot(int J, long long n, const cpx<T>* V, long long vstride, int cnt, const cpx<T>* w,
+                  double* partial, double* H, long long hs, int m, int col, bool add, const int* active,
+                  cudaStream_t st);
+// w_j -= sum_l h_{j,l} V_l (h = H column col, pass `pass` coefficients), and,
+// if nrm != null, the per-chunk partial sums of |w_j|^2 after the update
+// into nrm_partial[j][GM_CH]; the reduce writes sqrt into nrm[j * ns].
+// coef: per-frequency contiguous complex coefficients (frequency j at
+// coef + j * cs_j), at most 128 of them.
+template <class T>
+void launch_bmaxpy(int J, long long n, const cpx<T>* V, long long vstride, int cnt, cpx<T>* w,
+                   const double* coef, long long cs_j, double* nrm_partial, double* nrm, long long ns,
+                   const int* active, cudaStream_t st);
+// out[j][l] = H[j][l][col] for l < cnt (complex), out stride 128 per frequency
+void launch_hcol_gather(int J, int cnt, const double* H, long long hs, int m, int col, double* out,
+                        const int* active, cudaStream_t st);
+
+// H[j][l][col] += inc[j][l] (inc stride 128 per frequency)
+void launch_hcol_add(int J, int cnt, double* H, long long hs, int m, int col, const double* inc,
+                     const int* active, cudaStream_t st);
 
 // ---- outer FP64 vectors --------------------------------------------------
 // h[l] = <V_l, w> for l < cnt, V_l = V + l * n
