@@ -61,6 +61,7 @@ struct Engine {
   T* sink = nullptr;
 
   const T* n2d[PINT_MAXLEV] = {};  // per-level Q2 convection stencils (conv only)
+  const T* np2d = nullptr;         // finest-level Q1 convection stencils (conv only)
   void mg(int space, bool conv, const FieldJob* jobs, int njobs, cpx<T>* xb, const cpx<T>* bb, const int* active,
           int fields_per_job = 2);
   void cheb(int space, const FieldJob* jobs, int njobs, cpx<T>* xb, const cpx<T>* bb, const int* active,
@@ -281,6 +282,7 @@ template <class T>
 void Engine<T>::block_matvec(const BlkCoef* coef, const cpx<T>* X, cpx<T>* Out, const int* active) {
   BlkArgs<T> a{};
   a.tabs = tabs;
+  a.n2d = n2d[0];
   a.s = c->s;
   a.J = c->J;
   a.nu = c->p.nu;
@@ -315,6 +317,8 @@ void Engine<T>::block_prec(const cpx<T>* U, cpx<T>* Out, const int* active) {
   const long long lenv = 2LL * s.ns;
   ComboArgs<T> ca{};
   ca.tabs = tabs;
+  ca.n2d = n2d[0];
+  ca.np2d = np2d;
   ca.s = s;
   ca.J = J;
   ca.active = active;
@@ -381,6 +385,8 @@ void Engine<T>::block_prec(const cpx<T>* U, cpx<T>* Out, const int* active) {
   // X_p, the second swap's sign and the 1/tau factors
   ComboArgs<T> cq{};
   cq.tabs = tabs;
+  cq.n2d = n2d[0];
+  cq.np2d = np2d;
   cq.s = s;
   cq.J = J;
   cq.active = active;
@@ -541,6 +547,12 @@ bool setup_engine(pint_ctx* c, Engine<T>& e, size_t mg_jobs_q2, size_t mg_jobs_q
   const size_t mgws = std::max(mg_jobs_q2 * (size_t)c->lay2.per_job, mg_jobs_q1 * (size_t)c->lay1.per_job);
   const size_t chws = std::max(cheb_jobs_q2 * (size_t)c->cheb_per_q2, cheb_jobs_q1 * (size_t)c->cheb_per_q1);
   if (!c->alloc(&e.mgws, mgws * sizeof(cpx<T>)) || !c->alloc(&e.chebws, chws * sizeof(cpx<T>))) return false;
+  if (c->conv) {
+    T* t = nullptr;
+    if (!c->alloc(&t, (size_t)c->s.nq * 9 * sizeof(T))) return false;
+    launch_build_np2d<T>(c->t64, t, c->st);
+    e.np2d = t;
+  }
   if (c->conv)
     for (int l = 0; l < c->nlev; ++l) {
       const size_t n2 = 2 * (size_t)(c->N >> l) + 1, w6 = (n2 + 5) / 6;

@@ -257,6 +257,30 @@ __device__ __forceinline__ void bt_op(const T* __restrict__ bt, int n1, int n2, 
 // Real-valued variants for the FP64 time-domain KKT matvec reuse the complex
 // ones through a zero imaginary part; they are not on the hot path.
 
+// Index of Q2 node (ix, iy) in the class-blocked layout of a grid with n2
+// nodes per side: 36 residue classes (ix mod 6, iy mod 6) of w6 x w6 nodes,
+// w6 = ceil(n2 / 6).  The per-node convection tables use this order.
+__host__ __device__ __forceinline__ long long q2_blocked_index(int n2, int ix, int iy) {
+  const long long w6 = (n2 + 5) / 6;
+  return ((ix % 6) + 6 * (iy % 6)) * w6 * w6 + (iy / 6) * w6 + ix / 6;
+}
+
+// Convection from a per-node stencil row (W x W, rounded once from FP64):
+// sum_k row[k] x[neighbour k], neighbours clamped (their row entries are 0).
+template <class T, int W>
+__device__ __forceinline__ cpx<T> conv_row(const T* __restrict__ row, int n, int ix, int iy,
+                                           const cpx<T>* __restrict__ x) {
+  constexpr int H = W / 2;
+  cpx<T> acc = czero<T>();
+#pragma unroll
+  for (int dy = 0; dy < W; ++dy) {
+    const cpx<T>* r = x + (size_t)clampi(iy + dy - H, 0, n - 1) * n;
+#pragma unroll
+    for (int dx = 0; dx < W; ++dx) rfma(acc, row[dy * W + dx], r[clampi(ix + dx - H, 0, n - 1)]);
+  }
+  return acc;
+}
+
 __device__ __forceinline__ bool q2_interior(int ix, int iy, int n2) {
   return ix > 0 && iy > 0 && ix < n2 - 1 && iy < n2 - 1;
 }

@@ -33,6 +33,7 @@ struct BlkCoef {
 template <class T>
 struct BlkArgs {
   Tabs<T> tabs;
+  const T* n2d;  // per-node Q2 convection rows [blocked node][25] (conv only)
   Slots s;
   int J;
   double nu;
@@ -55,6 +56,8 @@ struct ComboRow {
 template <class T>
 struct ComboArgs {
   Tabs<T> tabs;
+  const T* n2d;   // per-node Q2 convection rows [blocked node][25] (conv only)
+  const T* np2d;  // per-node Q1 convection rows [node][9] (conv only)
   Slots s;
   int J, nrows, ncoef, space;  // space: 2 = Q2 field rows, 1 = Q1 field rows
   bool conv;

@@ -177,39 +177,28 @@ __global__ void __launch_bounds__(TPB) kkt_q1_kernel(KKTArgs A) {
 // complex M, K, N sums of one Q2 field
 template <class T, bool CONV>
 __device__ __forceinline__ void q2_mkn_c(const T* __restrict__ tab, int n2, int ix, int iy,
-                                         const cpx<T>* __restrict__ x, cpx<T>& m, cpx<T>& k, cpx<T>& nn) {
+                                         const cpx<T>* __restrict__ x, cpx<T>& m, cpx<T>& k, cpx<T>& nn,
+                                         const T* __restrict__ nrow) {
   const T* Mx = tab + (size_t)(0 * n2 + ix) * 5;
   const T* Kx = tab + (size_t)(1 * n2 + ix) * 5;
-  const T* Wx = tab + (size_t)(2 * n2 + ix) * 5;
-  const T* Xx = tab + (size_t)(3 * n2 + ix) * 5;
   const T* My = tab + (size_t)(0 * n2 + iy) * 5;
   const T* Ky = tab + (size_t)(1 * n2 + iy) * 5;
-  const T* Wy = tab + (size_t)(2 * n2 + iy) * 5;
-  const T* Xy = tab + (size_t)(3 * n2 + iy) * 5;
   m = k = nn = czero<T>();
 #pragma unroll
   for (int dy = 0; dy < 5; ++dy) {
     const cpx<T>* row = x + (size_t)clampi(iy + dy - 2, 0, n2 - 1) * n2;
-    cpx<T> sM = czero<T>(), sK = czero<T>(), sW = czero<T>(), sX = czero<T>();
+    cpx<T> sM = czero<T>(), sK = czero<T>();
 #pragma unroll
     for (int dx = 0; dx < 5; ++dx) {
       const cpx<T> v = row[clampi(ix + dx - 2, 0, n2 - 1)];
       rfma(sM, Mx[dx], v);
       rfma(sK, Kx[dx], v);
-      if (CONV) {
-        rfma(sW, Wx[dx], v);
-        rfma(sX, Xx[dx], v);
-      }
+      if (CONV) rfma(nn, nrow[dy * 5 + dx], v);
     }
     rfma(m, My[dy], sM);
     rfma(k, My[dy], sK);
     rfma(k, Ky[dy], sM);
-    if (CONV) {
-      rfma(nn, Xy[dy], sW);
-      rfma(nn, -Wy[dy], sX);
-    }
   }
-  nn = T(2) * nn;
 }
 
 template <class T, bool CONV>
@@ -236,14 +225,15 @@ __global__ void __launch_bounds__(TPB) blk_q2_kernel(BlkArgs<T> A) {
   const T g12 = T(cf.g12), g21 = T(cf.g21), dl = T(cf.dl), nu = T(A.nu);
   const T* tab = A.tabs.q2[0];
   cpx<T> bmx, bmy, bpx, bpy;
+  const T* nrow = CONV ? A.n2d + (size_t)q2_blocked_index(n2, ix, iy) * 25 : nullptr;
   bt_op<T>(A.tabs.bt, n1, n2, ix, iy, X + A.s.mu, bmx, bmy);
   bt_op<T>(A.tabs.bt, n1, n2, ix, iy, X + A.s.p, bpx, bpy);
 #pragma unroll
   for (int c = 0; c < 2; ++c) {
     const long long sv = c ? A.s.vy : A.s.vx, sl = c ? A.s.ly : A.s.lx;
     cpx<T> mv, kv, nv, ml, kl, nl;
-    q2_mkn_c<T, CONV>(tab, n2, ix, iy, X + sv, mv, kv, nv);
-    q2_mkn_c<T, CONV>(tab, n2, ix, iy, X + sl, ml, kl, nl);
+    q2_mkn_c<T, CONV>(tab, n2, ix, iy, X + sv, mv, kv, nv, nrow);
+    q2_mkn_c<T, CONV>(tab, n2, ix, iy, X + sl, ml, kl, nl, nrow);
     cpx<T> r1 = a11 * mv + a12 * ml;
     cpx<T> lt = nu * kl;
     if (CONV) lt = lt - nl;
@@ -296,6 +286,8 @@ __global__ void __launch_bounds__(TPB) combo_kernel(ComboArgs<T> A) {
   const bool unk = SP == 2 ? q2_interior(ix, iy, n) : q1_free(ix, iy);
   const OpCoef* cf = A.coef + (size_t)j * A.ncoef;
   const T* tab = SP == 2 ? A.tabs.q2[0] : A.tabs.q1[0];
+  const T* nrow = nullptr;
+  if (CONV) nrow = SP == 2 ? A.n2d + (size_t)q2_blocked_index(n, ix, iy) * 25 : A.np2d + (size_t)t * 9;
   for (int r = 0; r < A.nrows; ++r) {
     const ComboRow& R = A.rows[r];
     cpx<T> acc = czero<T>();
@@ -304,10 +296,14 @@ __global__ void __launch_bounds__(TPB) combo_kernel(ComboArgs<T> A) {
       for (int q = 0; q < R.nt; ++q) {
         const OpCoef oc = cf[R.tc[q]];
         const cpx<T> a = mkc<T>(T(oc.ar), T(oc.ai));
-        if (SP == 2)
-          acc = acc + q2_op<T, CONV>(tab, n, ix, iy, X + R.in_slot[q], a, T(oc.b), T(oc.c));
-        else
-          acc = acc + q1_op<T, CONV>(tab, n, ix, iy, X + R.in_slot[q], a, T(oc.b), T(oc.c));
+        const cpx<T>* xin = X + R.in_slot[q];
+        if (SP == 2) {
+          acc = acc + q2_op<T, false>(tab, n, ix, iy, xin, a, T(oc.b), T(0));
+          if (CONV && oc.c != 0.0) rfma(acc, T(oc.c), conv_row<T, 5>(nrow, n, ix, iy, xin));
+        } else {
+          acc = acc + q1_op<T, false>(tab, n, ix, iy, xin, a, T(oc.b), T(0));
+          if (CONV && oc.c != 0.0) rfma(acc, T(oc.c), conv_row<T, 3>(nrow, n, ix, iy, xin));
+        }
       }
     }
     O[R.out_slot + t] = acc;

@@ -390,6 +390,7 @@ __host__ __device__ __forceinline__ BLay make_blay(int n) {
   b.mg = (unsigned)((0x100000000ull + b.w6 - 1) / b.w6);
   return b;
 }
+// same order as q2_blocked_index (common.cuh), with the level's sizes cached
 __device__ __forceinline__ int bidx(const BLay& b, int ix, int iy) {
   return ((ix % 6) + 6 * (iy % 6)) * b.s + (iy / 6) * b.w6 + ix / 6;
 }
@@ -743,6 +744,28 @@ __global__ void build_n2d_kernel(Tabs<double> t64, int l, T* out) {
 }
 
 template <class T>
+__global__ void build_np2d_kernel(Tabs<double> t64, T* out) {
+  const int n = t64.N[0] + 1;
+  const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= (long long)n * n * 9) return;
+  const int k = (int)(q % 9);
+  const long long node = q / 9;
+  const int ix = (int)(node % n), iy = (int)(node / n);
+  const int dx = k % 3, dy = k / 3;
+  const double* tab = t64.q1[0];
+  const double wx = tab[(size_t)(2 * n + ix) * 3 + dx], xx = tab[(size_t)(3 * n + ix) * 3 + dx];
+  const double wy = tab[(size_t)(2 * n + iy) * 3 + dy], xy = tab[(size_t)(3 * n + iy) * 3 + dy];
+  out[q] = T(2.0 * (wx * xy - xx * wy));
+}
+
+template <class T>
+void launch_build_np2d(const Tabs<double>& t64, T* out, cudaStream_t st) {
+  const int n = t64.N[0] + 1;
+  const long long tot = (long long)n * n * 9;
+  build_np2d_kernel<T><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(t64, out);
+}
+
+template <class T>
 void launch_build_n2d(const Tabs<double>& t64, int l, T* out, cudaStream_t st) {
   const int n = 2 * t64.N[l] + 1;
   const long long tot = (long long)n * n * 25;
@@ -842,6 +865,8 @@ void launch_coarse_setup(const Tabs<double>& tabs, const OpCoef* ops, const int*
   coarse_setup_kernel<<<(nops + 63) / 64, 64, 0, st>>>(tabs, ops, op_space, op_conv, nops, inv, status);
 }
 
+template void launch_build_np2d<float>(const Tabs<double>&, float*, cudaStream_t);
+template void launch_build_np2d<double>(const Tabs<double>&, double*, cudaStream_t);
 template void launch_build_n2d<float>(const Tabs<double>&, int, float*, cudaStream_t);
 template void launch_build_n2d<double>(const Tabs<double>&, int, double*, cudaStream_t);
 template void launch_mg<float>(const MGLaunch<float>&, cudaStream_t);

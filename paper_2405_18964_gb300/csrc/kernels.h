@@ -83,6 +83,11 @@ void launch_cheb(const ChebLaunch<T>& L, cudaStream_t st);
 template <class T>
 void launch_build_n2d(const Tabs<double>& t64, int l, T* out, cudaStream_t st);
 
+// Per-node Q1 convection stencil N_p = 2 (W1 (x) X1 - X1 (x) W1) on the finest
+// pressure grid, FP64 -> T: out[(iy * n1 + ix) * 9 + dy * 3 + dx].
+template <class T>
+void launch_build_np2d(const Tabs<double>& t64, T* out, cudaStream_t st);
+
 // Coarse-grid inverses: for each op, the dense inverse of the operator on
 // the coarsest grid (FP64, Gauss-Jordan with partial pivoting).
 void launch_coarse_setup(const Tabs<double>& tabs, const OpCoef* ops, const int* op_space,
