@@ -22,7 +22,6 @@
 namespace pint {
 
 constexpr int MG_THREADS = 256;
-constexpr int MG_MINB = 4;  // resident CTAs per SM the register budget targets
 
 // ----------------------------------------------------------------------------
 // Stencil weights.  On the uniform grid the 2-D weights of a constant-
@@ -189,7 +188,7 @@ __device__ __forceinline__ void q2_pw(int f, int& base, float w[3]) {
 }
 
 template <class T, int SP, bool CONV, bool CW>
-__global__ void __launch_bounds__(MG_THREADS, MG_MINB) mg_kernel(MGLaunch<T> L) {
+__global__ void __launch_bounds__(1024, 1) mg_kernel(MGLaunch<T> L) {
   __shared__ cpx<T> sw[100];
   __shared__ cpx<T> sdi[9];
   __shared__ cpx<T>* Xs[PINT_MAXLEV][PINT_MAXF];
@@ -436,28 +435,26 @@ __device__ __forceinline__ cpx<T> stencil_b(const cpx<T>* __restrict__ w, const 
 template <class T, bool CONV, bool CW>
 __device__ void sor_colour_b(int n, const BLay& b, cpx<T>* X, const cpx<T>* B, const cpx<T>* sw, const cpx<T>* sdi,
                              const int* sdl, const T* n2d, T c, int colour, T omega) {
+  // the four classes of the colour (one per node type) in one parallel loop
   const int ccx = colour % 3, ccy = colour / 3;
-  const int tot = b.s;
-  for (int sub = 0; sub < 4; ++sub) {
+  for (int q = threadIdx.x; q < 4 * b.s; q += blockDim.x) {
+    const int sub = q / b.s, i = q - sub * b.s;
     const int rx = ccx + 3 * (sub & 1), ry = ccy + 3 * (sub >> 1);
+    const int my = udiv(i, b.mg), mx = i - my * b.w6;
+    const int ix = 6 * mx + rx, iy = 6 * my + ry;
+    if (ix < 1 || iy < 1 || ix > n - 2 || iy > n - 2) continue;
     const int type = (rx & 1) + 2 * (ry & 1), cls = rx + 6 * ry;
-    const cpx<T>* w = sw + type * 25;
-    const int* dl = sdl + cls * 25;
+    const int id = cls * b.s + i;
+    const cpx<T> ax = stencil_b<T, CONV, CW>(sw + type * 25, sdl + cls * 25,
+                                             CONV ? n2d + (size_t)id * 25 : nullptr, c, rx, ry, id, X);
+    const cpx<T> res = B[id] - ax;
     const cpx<T> di = sdi[type];
-    for (int q = threadIdx.x; q < tot; q += blockDim.x) {
-      const int my = udiv(q, b.mg), mx = q - my * b.w6;
-      const int ix = 6 * mx + rx, iy = 6 * my + ry;
-      if (ix < 1 || iy < 1 || ix > n - 2 || iy > n - 2) continue;
-      const int id = cls * b.s + q;
-      const cpx<T> ax = stencil_b<T, CONV, CW>(w, dl, CONV ? n2d + (size_t)id * 25 : nullptr, c, rx, ry, id, X);
-      const cpx<T> res = B[id] - ax;
-      X[id] = X[id] + omega * (CW ? res * di : di.x * res);
-    }
+    X[id] = X[id] + omega * (CW ? res * di : di.x * res);
   }
 }
 
 template <class T, bool CONV, bool CW>
-__global__ void __launch_bounds__(MG_THREADS, MG_MINB) mg_q2b_kernel(MGLaunch<T> L) {
+__global__ void __launch_bounds__(1024, 1) mg_q2b_kernel(MGLaunch<T> L) {
   __shared__ cpx<T> sw[100];
   __shared__ cpx<T> sdi[9];
   __shared__ int sdl[36 * 25];
@@ -623,10 +620,26 @@ __global__ void __launch_bounds__(MG_THREADS, MG_MINB) mg_q2b_kernel(MGLaunch<T>
   }
 }
 
+// CTA size from the number of jobs: fields are solved one per CTA, so with
+// fewer jobs than SMs each job gets more threads (the kernels are compiled
+// for a 64-register budget, valid for every size used here).
+int cta_threads(int njobs) {
+  static int nsm = 0;
+  if (!nsm) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (nsm <= 0) nsm = 1;
+  }
+  if (njobs <= nsm) return 1024;
+  if (njobs <= 2 * nsm) return 512;
+  return MG_THREADS;
+}
+
 template <class T>
 void launch_mg(const MGLaunch<T>& L, cudaStream_t st) {
   if (L.njobs <= 0) return;
-  dim3 grid(L.njobs), block(MG_THREADS);
+  dim3 grid(L.njobs), block(cta_threads(L.njobs));
   if (L.space == 2) {
     // one velocity field per CTA, class-blocked layout in the workspace
     if (L.conv)
@@ -651,7 +664,7 @@ void launch_mg(const MGLaunch<T>& L, cudaStream_t st) {
 // `steps` updates of x.
 // ---------------------------------------------------------------------------
 template <class T, int SP>
-__global__ void __launch_bounds__(MG_THREADS, MG_MINB) cheb_kernel(ChebLaunch<T> L) {
+__global__ void __launch_bounds__(1024, 1) cheb_kernel(ChebLaunch<T> L) {
   __shared__ cpx<T> sw[100];
   __shared__ cpx<T> sdi[9];
   const FieldJob jb = L.jobs[blockIdx.x];
@@ -718,10 +731,11 @@ __global__ void __launch_bounds__(MG_THREADS, MG_MINB) cheb_kernel(ChebLaunch<T>
 template <class T>
 void launch_cheb(const ChebLaunch<T>& L, cudaStream_t st) {
   if (L.njobs <= 0) return;
+  const int thr = cta_threads(L.njobs);
   if (L.space == 2)
-    cheb_kernel<T, 2><<<L.njobs, MG_THREADS, 0, st>>>(L);
+    cheb_kernel<T, 2><<<L.njobs, thr, 0, st>>>(L);
   else
-    cheb_kernel<T, 1><<<L.njobs, MG_THREADS, 0, st>>>(L);
+    cheb_kernel<T, 1><<<L.njobs, thr, 0, st>>>(L);
 }
 
 // ---------------------------------------------------------------------------
