@@ -106,6 +106,34 @@ class Problem:
         A = sp.kron(T1, self.S_M) + self.tau * sp.kron(T2, self.S_L) + self.tau * sp.kron(T3, self.S_LT)
         return A.tocsr()
 
+    def kkt_rows(self, x, block_rows):
+        """Selected block rows of A x (Eq. FinalA) without assembling A.
+
+        The Kronecker form is sum_t T_t (x) S_t with 2K x 2K time matrices
+        T_1 = [[tau I, E^T], [E, -tau/beta I]], T_2 = tau [[0, 0], [I, 0]],
+        T_3 = tau [[0, I], [0, 0]] and spatial blocks S_M, S_L, S_LT; block row
+        r of A x is sum_t sum_c T_t[r, c] S_t x_c.  block_rows: indices r in
+        [0, 2K) (r < K: adjoint-equation rows of time block r; r >= K: state
+        rows of block r - K).  Returns {r: vector of length nb}.
+        """
+        K, nb = self.K, self.nb
+        X = x.reshape(2 * K, nb)
+        E = self.time_matrix()
+        I = sp.eye(K, format="csr")
+        O = sp.csr_matrix((K, K))
+        T1 = sp.bmat([[self.tau * I, E.T], [E, -(self.tau / self.beta) * I]], format="csr")
+        T2 = self.tau * sp.bmat([[O, None], [I, O]], format="csr")
+        T3 = self.tau * sp.bmat([[O, I], [None, O]], format="csr")
+        out = {}
+        for r in block_rows:
+            y = np.zeros(nb)
+            for T, S in ((T1, self.S_M), (T2, self.S_L), (T3, self.S_LT)):
+                row = T.getrow(r)
+                for c, v in zip(row.indices, row.data):
+                    y += v * (S @ X[c])
+            out[r] = y
+        return out
+
     # -------------------------------------------------------- right-hand side
     def rhs(self, vd, f=None, v0=None):
         """Right-hand side from the backward-Euler equations (Sec. 2.2).

@@ -205,3 +205,15 @@ def test_layout_roundtrip():
     g = np.random.default_rng(6).standard_normal(P.nb * 2) + 0j
     np.testing.assert_array_equal(layout.to_oracle_freq(P, layout.from_oracle_freq(P, g)), g)
     assert layout.field_mask(P).sum() == P.nb * 2
+
+
+@pytest.mark.parametrize("P", [stokes(2, 5), oseen(2, 4)], ids=lambda P: f"{P.kind}")
+def test_kkt_rows_match_assembled_matrix(P):
+    """The row-wise evaluation used for full-size sampled checks agrees with
+    the assembled Eq. FinalA."""
+    x = np.random.default_rng(8).standard_normal(P.n)
+    y = P.kkt_matrix() @ x
+    rows = [0, 1, P.K - 1, P.K, 2 * P.K - 1]
+    got = P.kkt_rows(x, rows)
+    for r in rows:
+        np.testing.assert_allclose(got[r], y[r * P.nb:(r + 1) * P.nb], rtol=1e-13, atol=1e-13 * np.abs(y).max())
