@@ -61,6 +61,11 @@ def parse():
                     help="inner GMRES iteration cap (sizes the inner Krylov basis)")
     ap.add_argument("--only-timed", action="store_true",
                     help="run the warm-up and timed solves only (for profiler captures)")
+    ap.add_argument("--beta", type=float, default=None,
+                    help="solve for this one beta only (profiler captures: one handle on the device)")
+    ap.add_argument("--outer-restart", type=int, default=30,
+                    help="FGMRES restart length; smaller values shrink the device footprint for profiler "
+                         "captures (the reported metric uses 30)")
     return ap.parse_args()
 
 
@@ -115,6 +120,38 @@ def peaks():
     return 6800.0, "fallback"
 
 
+def peaks_bf16():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("bf16_tflops_sustained", 1700.0), "measured (sustained)"
+    return 1700.0, "fallback (sustained)"
+
+
+def dft_report(sizes, dft, bf16_peak):
+    """Time DFT of the FP32 preconditioner (split-BF16 x6 on tcgen05 for
+    n_t <= 256): algorithmic bytes (FP64 time slices in, complex FP32
+    Hermitian half out, or the reverse) and tensor flops as issued (six
+    128 x npad x 32 MMA products per tile and reduction chunk)."""
+    K, J, nblk = sizes.n_t, sizes.J, sizes.n_blk
+    npad = (K + 15) // 16 * 16
+    tiles = (nblk + 127) // 128
+    red = {"dft_fwd": (K + 31) // 32 * 32, "dft_inv": (2 * J + 31) // 32 * 32}
+    nbytes = K * nblk * 8 + J * nblk * 8
+    out = {"mode": "bf16x6 tcgen05" if K <= 256 else "simt", "bytes_per_launch": nbytes}
+    for d, c in dft.items():
+        if not c["timed"]:
+            continue
+        ms = c["ms"] / c["timed"]
+        fl = 6 * 2 * 128 * npad * red[d] * tiles
+        out[d] = {"avg_ms": round(ms, 4), "GBps": round(nbytes / (ms / 1e3) / 1e9, 1),
+                  "tensor_tflops_issued": round(fl / (ms / 1e3) / 1e12, 1),
+                  "tensor_frac_of_bf16_peak": round(fl / (ms / 1e3) / 1e12 / bf16_peak[0], 4)}
+    out["bf16_peak_tflops"] = bf16_peak[0]
+    out["bf16_peak_source"] = bf16_peak[1]
+    return out
+
+
 def dist_init():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     if ws <= 1:
@@ -150,13 +187,15 @@ def run_ours(a):
 
     def make(beta, prec, seed):
         p = binding.default_params(kind=W["kind"], level=W["level"], n_t=K, tau=tau, beta=beta, nu=W["nu"],
-                                   x0=W["x0"], x1=W["x1"], wind=W["wind"], prec=prec, inner_maxit=a.inner_maxit)
+                                   x0=W["x0"], x1=W["x1"], wind=W["wind"], prec=prec, inner_maxit=a.inner_maxit,
+                                   outer_restart=a.outer_restart)
         G = binding.Problem(p, stream=stream.cuda_stream)
         vd = inputs.desired_state(N, W["x0"], W["x1"], K, tau, T, seed)
         G.set_data(vd)
         return G, vd
 
-    probs = [make(b, 1, 1000 * rank + i) for i, b in enumerate(W["betas"])]
+    betas = W["betas"] if a.beta is None else [a.beta]
+    probs = [make(b, 1, 1000 * rank + i) for i, b in enumerate(betas)]
     n = probs[0][0].kkt_len
     x = torch.zeros(n, dtype=torch.float64, device="cuda")
 
@@ -170,7 +209,7 @@ def run_ours(a):
     torch.cuda.synchronize()
     # ---- timed region (device-resident inputs)
     for G, _ in probs:
-        G.profile_enable(["mg_q2"])
+        G.profile_enable(["mg_q2", "dft_fwd", "dft_inv"])
     clk = Clocks(dev)
     clk.start()
     if dist:
@@ -194,12 +233,15 @@ def run_ours(a):
         total_ms = float(t.item())
     prof = [G.profile_read() for G, _ in probs]
     mg = {k: sum(p["mg_q2"][k] for p in prof) for k in ("launches", "timed", "ms")}
+    dft = {d: {k: sum(p[d][k] for p in prof) for k in ("launches", "timed", "ms")} for d in ("dft_fwd", "dft_inv")}
     launches = sum(sum(c["launches"] for c in p.values()) for p in prof)
     value = a.steps * ws / (total_ms / 1e3)
     if a.only_timed:
         if rank == 0:
             print(json.dumps({"value": value, "unit": UNIT, "ms_per_step": total_ms / a.steps,
-                              "gpu_launches": int(launches)}), flush=True)
+                              "gpu_launches": int(launches),
+                              "mg_q2_avg_launch_ms": mg["ms"] / max(1, mg["timed"]),
+                              "dft_avg_ms": {d: c["ms"] / max(1, c["timed"]) for d, c in dft.items()}}), flush=True)
         return
 
     # ---- per-class shares from one fully profiled solve (outside the timed region)
@@ -266,6 +308,8 @@ def run_ours(a):
     if os.path.exists(tpath):
         traffic = json.load(open(tpath)).get("bytes_per_launch")
 
+    dft_line = dft_report(probs[0][0].sizes, dft, peaks_bf16())
+
     line = {
         "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": ws, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": round(total_ms / a.steps, 3), "higher_is_better": True,
@@ -290,6 +334,7 @@ def run_ours(a):
                      "frac": round(achieved / hbm, 4) if achieved else None, "traffic": traffic,
                      "avg_launch_ms": round(avg_ms, 4), "timed_launches": mg["timed"],
                      "algorithmic_bytes_per_launch": alg},
+        "dft": dft_line,
         "clocks": clocks,
     }
     if rank == 0 and not a.no_cpu_baseline:
@@ -380,6 +425,8 @@ def run_reference(a):
 
 def main():
     a = parse()
+    if not a.only_timed and (a.beta is not None or a.outer_restart != 30):
+        sys.exit("--beta and --outer-restart change the workload: use them with --only-timed only")
     if a.impl == "reference":
         run_reference(a)
         return

@@ -73,6 +73,21 @@ typedef enum { PINT_WIND_NONE = 0, PINT_WIND_RECIRC = 1 } pint_wind;
  * FP64 in both modes. */
 typedef enum { PINT_PREC_FP64 = 0, PINT_PREC_FP32 = 1 } pint_prec;
 
+/* How the FP32 preconditioner evaluates the time DFT and its inverse (the
+ * diagonalisation of the circulant C, Sec. 3.1): as a dense real
+ * contraction of the n_t x n_t real-DFT matrix with the n_t x n_blk block of
+ * time slices.
+ *  AUTO     FP32: BF16X6 when n_t <= 256, else CUDA cores.  FP64: CUDA cores.
+ *  SIMT     CUDA-core FMA in the preconditioner's precision.
+ *  BF16X6   tensor cores (tcgen05, BF16 operands, FP32 accumulation), each
+ *           operand split into three BF16 pieces and the six products whose
+ *           pieces sum to order <= 2 accumulated: about FP32 accuracy.
+ *  TF32X3   tensor cores (tcgen05, TF32 operands, FP32 accumulation), each
+ *           operand split into two TF32 pieces, three products.
+ * The tensor-core modes need n_t <= 256 and PINT_PREC_FP32; pint_create
+ * returns PINT_ERR_ARG otherwise. */
+typedef enum { PINT_DFT_AUTO = 0, PINT_DFT_SIMT = 1, PINT_DFT_BF16X6 = 2, PINT_DFT_TF32X3 = 3 } pint_dft_mode;
+
 typedef struct {
   int kind;            /* pint_kind                                          */
   int level;           /* N = 2^level elements per side, 1 <= level <= 10    */
@@ -96,6 +111,7 @@ typedef struct {
   double sor_omega;    /* SOR relaxation (1 = Gauss-Seidel)                  */
   int fixed_inner_its; /* > 0: run exactly this many inner GMRES iterations  */
   int linear;          /* 1: Algorithm 1 (no inner GMRES), 0: Algorithm 2/3  */
+  int dft_mode;        /* pint_dft_mode                                      */
 } pint_params;
 
 typedef struct {
@@ -242,6 +258,17 @@ typedef struct {
 pint_status pint_profile_enable(pint_handle h, unsigned mask);
 /* Synchronise the handle's stream and copy the counters out. */
 pint_status pint_profile_read(pint_handle h, pint_profile* out);
+
+/* Failure injection for tests (no GPU fault is involved).
+ * PINT_INJECT_DFT_STALL: the next tensor-core DFT launch of the handle arms
+ * its first pipeline barrier for 16 bytes more than its bulk copy delivers,
+ * so that every CTA's bounded wait (1 s) runs out; the kernel then waits
+ * (bounded) for its own copies, frees its tensor memory and returns, and the
+ * API call that ran it returns PINT_ERR_TIMEOUT.  The handle stays usable.
+ * Returns PINT_ERR_ARG for an unknown code or if the handle does not use the
+ * tensor-core DFT. */
+typedef enum { PINT_INJECT_DFT_STALL = 1 } pint_inject;
+pint_status pint_debug_inject(pint_handle h, int what);
 
 const char* pint_last_error(pint_handle h);
 

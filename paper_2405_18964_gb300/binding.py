@@ -33,7 +33,7 @@ class Params(ctypes.Structure):
                 ("inner_maxit", ctypes.c_int), ("mg_cycles", ctypes.c_int), ("mg_pre", ctypes.c_int),
                 ("mg_post", ctypes.c_int), ("cheb_steps", ctypes.c_int), ("uzawa_steps", ctypes.c_int),
                 ("uzawa_mu", ctypes.c_double), ("sor_omega", ctypes.c_double), ("fixed_inner_its", ctypes.c_int),
-                ("linear", ctypes.c_int)]
+                ("linear", ctypes.c_int), ("dft_mode", ctypes.c_int)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -80,6 +80,7 @@ _SIGS = {
     "pint_mg_apply_noalloc": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P, _P]),
     "pint_profile_enable": (ctypes.c_int, [_P, ctypes.c_uint]),
     "pint_profile_read": (ctypes.c_int, [_P, ctypes.POINTER(Profile)]),
+    "pint_debug_inject": (ctypes.c_int, [_P, ctypes.c_int]),
     "pint_last_error": (ctypes.c_char_p, [_P]),
 }
 
@@ -237,6 +238,10 @@ class Problem:
         _check(lib().pint_freq_block_solve(self.h, _dptr(rhat, "complex128", self.freq_len),
                                            _dptr(yhat, "complex128", self.freq_len), its), self.h)
         return list(its)
+
+    def debug_inject(self, what=1):
+        """Failure injection for tests (1: the next tensor-core DFT's bounded wait runs out)."""
+        _check(lib().pint_debug_inject(self.h, int(what)), self.h)
 
     def mg_apply_noalloc(self, which, j, x, y):
         """Multigrid on one field with the library's fixed scratch array (no allocation)."""

@@ -20,6 +20,7 @@
 #include <string>
 #include <vector>
 
+#include "dft_tc.h"
 #include "fields.h"
 #include "kernels.h"
 #include "krylov.h"
@@ -104,6 +105,8 @@ struct pint_ctx {
            *j_Mp2 = nullptr, *j_Kp2s = nullptr, *j_Mp2s = nullptr, *j_one = nullptr;
   int* d_active_one = nullptr;
   GmresState gs{};
+  DftTc tc{};              // tensor-core time DFT (FP32 preconditioner), scheme 0 = off
+  int* h_tcerr = nullptr;  // pinned copy of tc.err
 
   // outer FGMRES (FP64)
   double *oV = nullptr, *oZ = nullptr, *ob = nullptr, *ox = nullptr, *ot = nullptr, *opart = nullptr,
@@ -480,15 +483,41 @@ void Engine<T>::freq_solve(cpx<T>* Rin, cpx<T>* Out, int* its_host) {
   }
 }
 
+// Time DFT of a [K][nblk] FP64 vector into the Hermitian half [J][nblk] and
+// back (Sec. 3.1): tensor cores for the FP32 preconditioner when enabled,
+// else the CUDA-core kernels.
+template <class T>
+void dft_forward_any(pint_ctx* c, Engine<T>& e, const double* x, cpx<T>* X) {
+  PROF(c, PINT_PROF_DFT_FWD, 1);
+  launch_dft_forward<T>(c->K, c->J, c->s.nblk, x, X, e.cosk, e.sink, c->st);
+}
+template <>
+void dft_forward_any<float>(pint_ctx* c, Engine<float>& e, const double* x, cpx<float>* X) {
+  PROF(c, PINT_PROF_DFT_FWD, 1);
+  if (c->tc.scheme)
+    launch_dft_tc_forward(c->tc, c->s.nblk, x, X, c->st);
+  else
+    launch_dft_forward<float>(c->K, c->J, c->s.nblk, x, X, e.cosk, e.sink, c->st);
+}
+template <class T>
+void dft_inverse_any(pint_ctx* c, Engine<T>& e, const cpx<T>* X, double* y) {
+  PROF(c, PINT_PROF_DFT_INV, 1);
+  launch_dft_inverse<T>(c->K, c->J, c->s.nblk, X, y, e.cosk, e.sink, c->st);
+}
+template <>
+void dft_inverse_any<float>(pint_ctx* c, Engine<float>& e, const cpx<float>* X, double* y) {
+  PROF(c, PINT_PROF_DFT_INV, 1);
+  if (c->tc.scheme)
+    launch_dft_tc_inverse(c->tc, c->s.nblk, X, y, c->st);
+  else
+    launch_dft_inverse<float>(c->K, c->J, c->s.nblk, X, y, e.cosk, e.sink, c->st);
+}
+
 template <class T>
 void Engine<T>::apply(const double* r, double* z, int* its_host) {
-  {
-    PROF(c, PINT_PROF_DFT_FWD, 1);
-    launch_dft_forward<T>(c->K, c->J, c->s.nblk, r, R, cosk, sink, c->st);
-  }
+  dft_forward_any<T>(c, *this, r, R);
   freq_solve(R, Y, its_host);
-  PROF(c, PINT_PROF_DFT_INV, 1);
-  launch_dft_inverse<T>(c->K, c->J, c->s.nblk, Y, z, cosk, sink, c->st);
+  dft_inverse_any<T>(c, *this, Y, z);
 }
 
 // ============================================================================
@@ -507,6 +536,10 @@ bool valid_params(const pint_params* p, std::string& why) {
   if (p->wind == PINT_WIND_RECIRC && (p->x0 != -1.0 || p->x1 != 1.0))
     return why = "the recirculating wind requires the domain [-1,1]^2", false;
   if (p->prec != PINT_PREC_FP64 && p->prec != PINT_PREC_FP32) return why = "unknown precision", false;
+  if (p->dft_mode < PINT_DFT_AUTO || p->dft_mode > PINT_DFT_TF32X3) return why = "unknown dft_mode", false;
+  if ((p->dft_mode == PINT_DFT_BF16X6 || p->dft_mode == PINT_DFT_TF32X3) &&
+      (p->prec != PINT_PREC_FP32 || p->n_t > 256))
+    return why = "tensor-core DFT modes need prec = PINT_PREC_FP32 and n_t <= 256", false;
   if (p->outer_restart < 1 || p->outer_restart > 200) return why = "outer_restart must be in [1, 200]", false;
   if (p->outer_maxit < 1) return why = "outer_maxit must be positive", false;
   if (!(p->outer_tol > 0)) return why = "outer_tol must be positive", false;
@@ -817,6 +850,26 @@ pint_status build(pint_ctx* c) {
   else
     ok = setup_engine<double>(c, c->e64, mgq2, mgq1, chq2, chq1);
   if (!ok) return c->fail(PINT_ERR_OOM, "device allocation failed (preconditioner workspace)");
+  {
+    const int mode = p.dft_mode == PINT_DFT_AUTO ? (c->fp32 && c->K <= 256 ? PINT_DFT_BF16X6 : PINT_DFT_SIMT)
+                                                 : p.dft_mode;
+    if (mode == PINT_DFT_BF16X6 || mode == PINT_DFT_TF32X3) {
+      DftTc& d = c->tc;
+      dft_tc_geometry(c->K, mode == PINT_DFT_BF16X6 ? DFT_TC_BF16X6 : DFT_TC_TF32X3, &d);
+      std::vector<unsigned char> tf(dft_tc_table_bytes(c->K, d.scheme, false)),
+          ti(dft_tc_table_bytes(c->K, d.scheme, true));
+      dft_tc_build_table(c->K, d.scheme, false, tf.data());
+      dft_tc_build_table(c->K, d.scheme, true, ti.data());
+      unsigned char *bf = nullptr, *bi = nullptr;
+      if (!c->upload(&bf, tf) || !c->upload(&bi, ti) || !c->alloc(&d.err, sizeof(int)))
+        return c->fail(PINT_ERR_OOM, "device allocation failed (DFT tables)");
+      d.bf = bf;
+      d.bi = bi;
+      if (!c->cu(cudaMemsetAsync(d.err, 0, sizeof(int), c->st), "DFT error flag") ||
+          !c->cu(cudaMallocHost(&c->h_tcerr, sizeof(int)), "pinned host buffer"))
+        return PINT_ERR_CUDA;
+    }
+  }
 
   // ---- outer FGMRES workspace (FP64)
   const size_t n = (size_t)c->K * s.nblk;
@@ -834,6 +887,18 @@ pint_status build(pint_ctx* c) {
   return PINT_OK;
 }
 
+// Reads (and clears) the tensor-core DFT's device error flag: nonzero means a
+// bounded wait inside the kernel gave up and its output is not valid.
+pint_status tc_status(pint_ctx* c) {
+  if (!c->tc.scheme) return PINT_OK;
+  if (!c->cu(cudaMemcpyAsync(c->h_tcerr, c->tc.err, sizeof(int), cudaMemcpyDeviceToHost, c->st), "DFT status") ||
+      !c->cu(cudaStreamSynchronize(c->st), "DFT status"))
+    return PINT_ERR_CUDA;
+  if (*c->h_tcerr == 0) return PINT_OK;
+  cudaMemsetAsync(c->tc.err, 0, sizeof(int), c->st);
+  return c->fail(PINT_ERR_TIMEOUT, "tensor-core DFT: a bounded wait gave up; results are not valid");
+}
+
 void free_ctx(pint_ctx* c) {
   if (!c) return;
   if (c->st) cudaStreamSynchronize(c->st);
@@ -842,6 +907,7 @@ void free_ctx(pint_ctx* c) {
   for (void* v : c->allocs) cudaFree(v);
   if (c->h_pinned) cudaFreeHost(c->h_pinned);
   if (c->h_count) cudaFreeHost(c->h_count);
+  if (c->h_tcerr) cudaFreeHost(c->h_tcerr);
   delete c;
 }
 
@@ -1039,6 +1105,7 @@ void pint_default_params(pint_params* p) {
   p->sor_omega = 1.0;
   p->fixed_inner_its = 0;
   p->linear = 0;
+  p->dft_mode = PINT_DFT_AUTO;
 }
 
 pint_status pint_create(const pint_params* p, void* stream, pint_handle* out) {
@@ -1174,7 +1241,8 @@ pint_status pint_apply_preconditioner(pint_handle h, const double* r, double* z)
     return PINT_ERR_CUDA;
   { PROF(h, PINT_PROF_OTHER, 1); launch_mask_blocks(h->s, h->K, 1, h->ot, h->st); }
   apply_prec(h, h->ot, z, nullptr);
-  return h->launched("preconditioner") ? PINT_OK : PINT_ERR_CUDA;
+  if (!h->launched("preconditioner")) return PINT_ERR_CUDA;
+  return tc_status(h);
 }
 
 pint_status pint_solve(pint_handle h, double* x, pint_solve_info* info) {
@@ -1191,7 +1259,8 @@ pint_status pint_solve(pint_handle h, double* x, pint_solve_info* info) {
   if (!h->cu(cudaMemcpyAsync(x, h->ox, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->st), "copy x") ||
       !h->cu(cudaStreamSynchronize(h->st), "solve"))
     return PINT_ERR_CUDA;
-  return rc;
+  const pint_status ts = tc_status(h);
+  return ts != PINT_OK ? ts : rc;
 }
 
 pint_status pint_solve_host(pint_handle h, double* x_host, pint_solve_info* info) {
@@ -1208,7 +1277,8 @@ pint_status pint_solve_host(pint_handle h, double* x_host, pint_solve_info* info
   if (!h->cu(cudaMemcpyAsync(x_host, h->ox, sizeof(double) * n, cudaMemcpyDeviceToHost, h->st), "download x") ||
       !h->cu(cudaStreamSynchronize(h->st), "solve"))
     return PINT_ERR_CUDA;
-  return rc;
+  const pint_status ts = tc_status(h);
+  return ts != PINT_OK ? ts : rc;
 }
 
 }  // extern "C"
@@ -1241,18 +1311,20 @@ pint_status dft_fwd_T(pint_ctx* c, Engine<T>& e, const double* x, double* xhat) 
   const size_t n = (size_t)c->K * c->s.nblk;
   cudaMemcpyAsync(c->ot, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->st);
   { PROF(c, PINT_PROF_OTHER, 1); launch_mask_blocks(c->s, c->K, 1, c->ot, c->st); }
-  launch_dft_forward<T>(c->K, c->J, c->s.nblk, c->ot, e.R, e.cosk, e.sink, c->st);
+  dft_forward_any<T>(c, e, c->ot, e.R);
   from_T<T>(c, e.R, xhat, (size_t)c->J * c->s.nblk);
-  return c->launched("dft forward") ? PINT_OK : PINT_ERR_CUDA;
+  if (!c->launched("dft forward")) return PINT_ERR_CUDA;
+  return tc_status(c);
 }
 
 template <class T>
 pint_status dft_inv_T(pint_ctx* c, Engine<T>& e, const double* xhat, double* x) {
   const size_t fl = (size_t)c->J * c->s.nblk;
   to_T<T>(c, xhat, e.R, fl);
-  launch_dft_inverse<T>(c->K, c->J, c->s.nblk, e.R, x, e.cosk, e.sink, c->st);
+  dft_inverse_any<T>(c, e, e.R, x);
   { PROF(c, PINT_PROF_OTHER, 1); launch_mask_blocks(c->s, c->K, 1, x, c->st); }
-  return c->launched("dft inverse") ? PINT_OK : PINT_ERR_CUDA;
+  if (!c->launched("dft inverse")) return PINT_ERR_CUDA;
+  return tc_status(c);
 }
 
 template <class T>
@@ -1378,6 +1450,14 @@ pint_status pint_component_apply(pint_handle h, int which, int j, const double* 
   if (j < 0 || j >= h->J) return h->fail(PINT_ERR_ARG, "frequency index out of range");
   return h->fp32 ? component_T<float>(h, h->e32, which, j, in, out)
                  : component_T<double>(h, h->e64, which, j, in, out);
+}
+
+pint_status pint_debug_inject(pint_handle h, int what) {
+  if (!h) return g_err = "null handle", PINT_ERR_ARG;
+  if (what != PINT_INJECT_DFT_STALL) return h->fail(PINT_ERR_ARG, "unknown injection code");
+  if (!h->tc.scheme) return h->fail(PINT_ERR_ARG, "this handle does not use the tensor-core DFT");
+  h->tc.stall_next = true;
+  return PINT_OK;
 }
 
 pint_status pint_profile_enable(pint_handle h, unsigned mask) {

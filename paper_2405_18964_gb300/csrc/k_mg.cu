@@ -395,32 +395,44 @@ __device__ __forceinline__ int bidx(const BLay& b, int ix, int iy) {
 }
 __device__ __forceinline__ int udiv(unsigned q, unsigned mg) { return (int)__umulhi(q, mg); }
 
-// Neighbour offsets of one level: delta[cls * 25 + (dy + 2) * 5 + (dx + 2)].
-__device__ void level_deltas(const BLay& b, int* delta) {
-  for (int q = threadIdx.x; q < 36 * 25; q += blockDim.x) {
-    const int cls = q / 25, k = q % 25;
-    const int rx = cls % 6, ry = cls / 6, dx = k % 5 - 2, dy = k / 5 - 2;
-    const int ax = rx + dx, ay = ry + dy;
-    const int sx = ax < 0 ? -1 : (ax >= 6 ? 1 : 0), sy = ay < 0 ? -1 : (ay >= 6 ? 1 : 0);
-    const int rxn = ax - 6 * sx, ryn = ay - 6 * sy;
-    delta[q] = ((rxn - rx) + 6 * (ryn - ry)) * b.s + sy * b.w6 + sx;
-  }
+// Neighbour offsets.  A node of class (rx, ry) at sub-grid position (mx, my)
+// has blocked index id = (rx + 6 ry) s + my w6 + mx; its neighbour (dx, dy)
+// lies at id + xoff(rx, dx) + yoff(ry, dy) with
+//   xoff = dx s + sx (1 - 6 s),   sx = [rx + dx >= 6] - [rx + dx < 0],
+//   yoff = 6 dy s + sy (w6 - 36 s), sy likewise,
+// i.e. the class changes by dx (wrapping mod 6) and the sub-grid column by sx.
+__device__ __forceinline__ int xoff(const BLay& b, int rx, int dx) {
+  const int a = rx + dx;
+  const int sx = (a >= 6) - (a < 0);
+  return dx * b.s + sx * (1 - 6 * b.s);
 }
+__device__ __forceinline__ int yoff(const BLay& b, int ry, int dy) {
+  const int a = ry + dy;
+  const int sy = (a >= 6) - (a < 0);
+  return 6 * dy * b.s + sy * (b.w6 - 36 * b.s);
+}
+// Separable parts of the blocked index of node (ix, iy), ix, iy >= 0:
+// bidx = xpart(ix) + ypart(iy).
+__device__ __forceinline__ int xpart(const BLay& b, int ix) { return (ix % 6) * b.s + ix / 6; }
+__device__ __forceinline__ int ypart(const BLay& b, int iy) { return 6 * (iy % 6) * b.s + (iy / 6) * b.w6; }
 
 // (A x) at the node with blocked index id in class (rx, ry).
 template <class T, bool CONV, bool CW>
-__device__ __forceinline__ cpx<T> stencil_b(const cpx<T>* __restrict__ w, const int* __restrict__ dl,
-                                            const T* __restrict__ nrow, T c, int rx, int ry, int id,
-                                            const cpx<T>* __restrict__ x) {
+__device__ __forceinline__ cpx<T> stencil_b(const cpx<T>* __restrict__ w, const BLay& b, const T* __restrict__ nrow,
+                                            T c, int rx, int ry, int id, const cpx<T>* __restrict__ x) {
+  int xo[5];
+#pragma unroll
+  for (int dx = -2; dx <= 2; ++dx) xo[dx + 2] = xoff(b, rx, dx);
   cpx<T> acc = czero<T>(), accn = czero<T>();
 #pragma unroll
   for (int dy = -2; dy <= 2; ++dy) {
     if ((ry & 1) && (dy == -2 || dy == 2)) continue;  // midpoint rows couple to +-1 only
+    const cpx<T>* row = x + id + yoff(b, ry, dy);
 #pragma unroll
     for (int dx = -2; dx <= 2; ++dx) {
       if ((rx & 1) && (dx == -2 || dx == 2)) continue;
       const int k = (dy + 2) * 5 + (dx + 2);
-      const cpx<T> v = x[id + dl[k]];
+      const cpx<T> v = row[xo[dx + 2]];
       if (CW)
         acc = acc + w[k] * v;
       else
@@ -433,23 +445,46 @@ __device__ __forceinline__ cpx<T> stencil_b(const cpx<T>* __restrict__ w, const 
 }
 
 template <class T, bool CONV, bool CW>
+__device__ __forceinline__ void sor_node_b(int n, const BLay& b, int ccx, int ccy, int q, int& id, int& type,
+                                           int& rx, int& ry, bool& valid) {
+  const int sub = q / b.s, i = q - sub * b.s;
+  rx = ccx + 3 * (sub & 1);
+  ry = ccy + 3 * (sub >> 1);
+  const int my = udiv(i, b.mg), mx = i - my * b.w6;
+  const int ix = 6 * mx + rx, iy = 6 * my + ry;
+  valid = q < 4 * b.s && ix >= 1 && iy >= 1 && ix <= n - 2 && iy <= n - 2;
+  type = (rx & 1) + 2 * (ry & 1);
+  id = (rx + 6 * ry) * b.s + i;
+}
+
+template <class T, bool CONV, bool CW>
 __device__ void sor_colour_b(int n, const BLay& b, cpx<T>* X, const cpx<T>* B, const cpx<T>* sw, const cpx<T>* sdi,
-                             const int* sdl, const T* n2d, T c, int colour, T omega) {
-  // the four classes of the colour (one per node type) in one parallel loop
+                             const T* n2d, T c, int colour, T omega) {
+  // the four classes of the colour (one per node type) in one parallel loop;
+  // same-colour nodes do not couple, so two nodes per thread are evaluated
+  // before either is written (independent loads in flight)
   const int ccx = colour % 3, ccy = colour / 3;
-  for (int q = threadIdx.x; q < 4 * b.s; q += blockDim.x) {
-    const int sub = q / b.s, i = q - sub * b.s;
-    const int rx = ccx + 3 * (sub & 1), ry = ccy + 3 * (sub >> 1);
-    const int my = udiv(i, b.mg), mx = i - my * b.w6;
-    const int ix = 6 * mx + rx, iy = 6 * my + ry;
-    if (ix < 1 || iy < 1 || ix > n - 2 || iy > n - 2) continue;
-    const int type = (rx & 1) + 2 * (ry & 1), cls = rx + 6 * ry;
-    const int id = cls * b.s + i;
-    const cpx<T> ax = stencil_b<T, CONV, CW>(sw + type * 25, sdl + cls * 25,
-                                             CONV ? n2d + (size_t)id * 25 : nullptr, c, rx, ry, id, X);
-    const cpx<T> res = B[id] - ax;
-    const cpx<T> di = sdi[type];
-    X[id] = X[id] + omega * (CW ? res * di : di.x * res);
+  const int step = blockDim.x;
+  for (int q0 = threadIdx.x; q0 < 4 * b.s; q0 += 2 * step) {
+    int id0, id1, t0, t1, rx0, ry0, rx1, ry1;
+    bool v0, v1;
+    sor_node_b<T, CONV, CW>(n, b, ccx, ccy, q0, id0, t0, rx0, ry0, v0);
+    sor_node_b<T, CONV, CW>(n, b, ccx, ccy, q0 + step, id1, t1, rx1, ry1, v1);
+    cpx<T> r0 = czero<T>(), r1 = czero<T>();
+    if (v0)
+      r0 = B[id0] - stencil_b<T, CONV, CW>(sw + t0 * 25, b, CONV ? n2d + (size_t)id0 * 25 : nullptr, c, rx0, ry0,
+                                            id0, X);
+    if (v1)
+      r1 = B[id1] - stencil_b<T, CONV, CW>(sw + t1 * 25, b, CONV ? n2d + (size_t)id1 * 25 : nullptr, c, rx1, ry1,
+                                            id1, X);
+    if (v0) {
+      const cpx<T> di = sdi[t0];
+      X[id0] = X[id0] + omega * (CW ? r0 * di : di.x * r0);
+    }
+    if (v1) {
+      const cpx<T> di = sdi[t1];
+      X[id1] = X[id1] + omega * (CW ? r1 * di : di.x * r1);
+    }
   }
 }
 
@@ -457,7 +492,6 @@ template <class T, bool CONV, bool CW>
 __global__ void __launch_bounds__(1024, 1) mg_q2b_kernel(MGLaunch<T> L) {
   __shared__ cpx<T> sw[100];
   __shared__ cpx<T> sdi[9];
-  __shared__ int sdl[36 * 25];
   const FieldJob jb = L.jobs[blockIdx.x];
   if (L.active && !L.active[jb.freq]) return;
   const OpCoef oc = L.ops[jb.op];
@@ -499,11 +533,10 @@ __global__ void __launch_bounds__(1024, 1) mg_q2b_kernel(MGLaunch<T> L) {
       cpx<T>* X = Xl(l);
       const cpx<T>* B = Bl(l);
       level_weights<T, 2>(L.t64, l, n, a, bb, sw, sdi);
-      level_deltas(b, sdl);
       __syncthreads();
       for (int s = 0; s < L.pre; ++s)
         for (int col = 0; col < 9; ++col) {
-          sor_colour_b<T, CONV, CW>(n, b, X, B, sw, sdi, sdl, n2d, cc, col, omega);
+          sor_colour_b<T, CONV, CW>(n, b, X, B, sw, sdi, n2d, cc, col, omega);
           __syncthreads();
         }
       // residual over all classes (non-unknown and padding slots get 0)
@@ -515,7 +548,7 @@ __global__ void __launch_bounds__(1024, 1) mg_q2b_kernel(MGLaunch<T> L) {
         const int ix = 6 * mx + rx, iy = 6 * my + ry;
         cpx<T> r = czero<T>();
         if (ix >= 1 && iy >= 1 && ix <= n - 2 && iy <= n - 2)
-          r = B[q] - stencil_b<T, CONV, CW>(sw + ((rx & 1) + 2 * (ry & 1)) * 25, sdl + cls * 25,
+          r = B[q] - stencil_b<T, CONV, CW>(sw + ((rx & 1) + 2 * (ry & 1)) * 25, b,
                                             CONV ? n2d + (size_t)q * 25 : nullptr, cc, rx, ry, q, X);
         R[q] = r;
       }
@@ -532,16 +565,26 @@ __global__ void __launch_bounds__(1024, 1) mg_q2b_kernel(MGLaunch<T> L) {
         const int ix = 6 * mx + rx, iy = 6 * my + ry;
         cpx<T> acc = czero<T>();
         if (ix >= 1 && iy >= 1 && ix <= nc - 2 && iy <= nc - 2) {
+          // fine nodes 2 ix + ox, 2 iy + oy (nonzero weights: |o| <= 1, and 3 at coarse vertices)
+          const int fx = 2 * ix, fy = 2 * iy;
+          int xp[7], yp[7];
+#pragma unroll
+          for (int o = -3; o <= 3; ++o) {
+            xp[o + 3] = (q2_rw(ix, o) != 0.f) ? xpart(b, fx + o) : 0;
+            yp[o + 3] = (q2_rw(iy, o) != 0.f) ? ypart(b, fy + o) : 0;
+          }
 #pragma unroll
           for (int oy = -3; oy <= 3; ++oy) {
             const T wy = T(q2_rw(iy, oy));
             if (wy == T(0)) continue;
+            cpx<T> s = czero<T>();
 #pragma unroll
             for (int ox = -3; ox <= 3; ++ox) {
               const T wx = T(q2_rw(ix, ox));
               if (wx == T(0)) continue;
-              rfma(acc, wx * wy, R[bidx(b, 2 * ix + ox, 2 * iy + oy)]);
+              rfma(s, wx, R[xp[ox + 3] + yp[oy + 3]]);
             }
+            rfma(acc, wy, s);
           }
         }
         Bc[q] = acc;
@@ -577,7 +620,6 @@ __global__ void __launch_bounds__(1024, 1) mg_q2b_kernel(MGLaunch<T> L) {
       const cpx<T>* B = Bl(l);
       const cpx<T>* Xc = Xl(l + 1);
       level_weights<T, 2>(L.t64, l, n, a, bb, sw, sdi);
-      level_deltas(b, sdl);
       // prolongation onto the fine level
       for (int q = threadIdx.x; q < 36 * b.s; q += blockDim.x) {
         const int cls = q / b.s, i = q - cls * b.s;
@@ -589,22 +631,30 @@ __global__ void __launch_bounds__(1024, 1) mg_q2b_kernel(MGLaunch<T> L) {
         float wx[3], wy[3];
         q2_pw(ix, bx, wx);
         q2_pw(iy, by, wy);
+        int xp[3], yp[3];
+#pragma unroll
+        for (int t = 0; t < 3; ++t) {
+          xp[t] = wx[t] != 0.f ? xpart(bc, bx + t) : 0;
+          yp[t] = wy[t] != 0.f ? ypart(bc, by + t) : 0;
+        }
         cpx<T> acc = czero<T>();
 #pragma unroll
         for (int ty = 0; ty < 3; ++ty) {
           if (wy[ty] == 0.f) continue;
+          cpx<T> s = czero<T>();
 #pragma unroll
           for (int tx = 0; tx < 3; ++tx) {
             if (wx[tx] == 0.f) continue;
-            rfma(acc, T(wx[tx] * wy[ty]), Xc[bidx(bc, bx + tx, by + ty)]);
+            rfma(s, T(wx[tx]), Xc[xp[tx] + yp[ty]]);
           }
+          rfma(acc, T(wy[ty]), s);
         }
         X[q] = X[q] + acc;
       }
       __syncthreads();
       for (int s = 0; s < L.post; ++s)
         for (int col = 8; col >= 0; --col) {
-          sor_colour_b<T, CONV, CW>(n, b, X, B, sw, sdi, sdl, n2d, cc, col, omega);
+          sor_colour_b<T, CONV, CW>(n, b, X, B, sw, sdi, n2d, cc, col, omega);
           __syncthreads();
         }
     }

@@ -6,6 +6,13 @@ from paper_2405_18964_gb300 import binding
 
 FP64_TOL = 1e-12   # FP64 preconditioner / component parity (relative, max-norm)
 FP32_TOL = 1e-5    # FP32 preconditioner / component parity
+# FP64 bar for pressure values that pass through the multigrid on the
+# corner-pinned pressure Laplacian K_p at 64 x 64: evaluating the same K_p in
+# band form (M1 X K1^T + K1 X M1^T) instead of assembled rows moves the
+# oracle's own 4-V-cycle result by 2.7e-12 (tests/test_oracle_inexact.py::
+# test_pressure_multigrid_rounding_spread), so differences of that size are
+# evaluation order, not error.  Velocity and multiplier parts keep FP64_TOL.
+KP_FP64_TOL = 4e-12
 
 
 def make_pair(kind, level, K, beta=1e-2, nu=1e-2, prec=0, T=1.0, **kw):
@@ -38,6 +45,20 @@ def relerr(a, b):
 def to_dev(a, dtype="float64"):
     import torch
     return torch.from_numpy(np.ascontiguousarray(a)).to(device="cuda", dtype=getattr(torch, dtype))
+
+
+def part_slices(P):
+    """Slices of the oracle's frequency-block vector (v, lambda, p, mu)."""
+    nv, npf = 2 * len(P.vi), len(P.pf)
+    return {"v": slice(0, nv), "lam": slice(nv, 2 * nv), "p": slice(2 * nv, 2 * nv + npf),
+            "mu": slice(2 * nv + npf, None)}
+
+
+def part_errors(P, got, ref):
+    """Max-norm error of each part relative to the largest entry of ref."""
+    den = np.abs(ref).max()
+    den = den if den > 0 else 1.0
+    return {k: float(np.abs(got[sl] - ref[sl]).max() / den) for k, sl in part_slices(P).items()}
 
 
 def freq_blocks(P, Xh):

@@ -50,4 +50,11 @@ def test_default_params_and_argument_validation():
     bad = binding.default_params(kind=1, wind=1, x0=0.0, x1=1.0)
     assert binding.lib().pint_create(ctypes.byref(bad), None, ctypes.byref(h)) == 1
     assert b"[-1,1]" in binding.lib().pint_last_error(None)
+    bad = binding.default_params(prec=0, dft_mode=2)          # tensor-core DFT needs FP32
+    assert binding.lib().pint_create(ctypes.byref(bad), None, ctypes.byref(h)) == 1
+    assert b"dft" in binding.lib().pint_last_error(None).lower()
+    bad = binding.default_params(prec=1, dft_mode=3, n_t=300)  # and n_t <= 256
+    assert binding.lib().pint_create(ctypes.byref(bad), None, ctypes.byref(h)) == 1
+    bad = binding.default_params(dft_mode=7)
+    assert binding.lib().pint_create(ctypes.byref(bad), None, ctypes.byref(h)) == 1
     assert binding.lib().pint_destroy(None) == 0

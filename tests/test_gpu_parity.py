@@ -51,10 +51,13 @@ def test_rhs(kind, level, K):
     assert relerr(layout.to_oracle_time(P, b.cpu().numpy().reshape(K, -1)), bo) <= 1e-14
 
 
-@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("prec,dft_mode", [(0, 0), (1, 1), (1, 2), (1, 3)],
+                         ids=["fp64", "fp32-simt", "fp32-bf16x6", "fp32-tf32x3"])
 @pytest.mark.parametrize("kind,level,K", KINDS, ids=IDS)
-def test_dft_forward_inverse(kind, level, K, prec):
-    P, G = make_pair(kind, level, K, prec=prec)
+def test_dft_forward_inverse(kind, level, K, prec, dft_mode):
+    """Both DFT directions against numpy's FFT; the FP32 modes on CUDA cores
+    and on the tensor cores (split BF16 x6 and TF32 x3 operands)."""
+    P, G = make_pair(kind, level, K, prec=prec, dft_mode=dft_mode)
     x = inputs.random_vector((K, layout.block_len(P)), 3)
     x[:, ~layout.field_mask(P)] = 0.0
     xh = torch.zeros(G.freq_len, dtype=torch.complex128, device="cuda")
