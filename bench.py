@@ -152,17 +152,40 @@ def dft_report(sizes, dft, bf16_peak):
     return out
 
 
-def dist_init():
+def dist_init(backend="nccl"):
+    """Replicas: one process per GPU under torch.distributed.run; the only
+    collectives are the barrier around the timed region and the max over
+    ranks of its duration (no collective on the data path)."""
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     if ws <= 1:
         return 0, 1, None
     import torch.distributed as dist
     rank = int(os.environ["RANK"])
-    local = int(os.environ.get("LOCAL_RANK", rank))
-    import torch
-    torch.cuda.set_device(local)
-    dist.init_process_group("nccl", init_method="env://")
+    if backend == "nccl":
+        import torch
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", rank)))
+    dist.init_process_group(backend, init_method="env://")
     return rank, ws, dist
+
+
+def max_over_ranks(x, dist, device="cuda"):
+    """The largest value of x over all ranks (the job's timed duration)."""
+    if not dist:
+        return x
+    import torch
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_seeds(rank, count):
+    """Data seeds of one replica's problems: distinct across ranks."""
+    return [1000 * rank + i for i in range(count)]
+
+
+def whole_job_rate(steps, world_size, max_ms):
+    """Units all ranks processed divided by the slowest rank's time."""
+    return steps * world_size / (max_ms / 1e3)
 
 
 def algorithmic_bytes_mg_q2(sizes, nlaunch_jobs, cycles, bw):
@@ -195,7 +218,7 @@ def run_ours(a):
         return G, vd
 
     betas = W["betas"] if a.beta is None else [a.beta]
-    probs = [make(b, 1, 1000 * rank + i) for i, b in enumerate(betas)]
+    probs = [make(b, 1, sd) for b, sd in zip(betas, replica_seeds(rank, len(betas)))]
     n = probs[0][0].kkt_len
     x = torch.zeros(n, dtype=torch.float64, device="cuda")
 
@@ -227,15 +250,12 @@ def run_ours(a):
     clocks = clk.stop()
     lat = [ev[i].elapsed_time(ev[i + 1]) for i in range(a.steps)]
     total_ms = ev[0].elapsed_time(ev[-1])
-    if dist:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, dist)
     prof = [G.profile_read() for G, _ in probs]
     mg = {k: sum(p["mg_q2"][k] for p in prof) for k in ("launches", "timed", "ms")}
     dft = {d: {k: sum(p[d][k] for p in prof) for k in ("launches", "timed", "ms")} for d in ("dft_fwd", "dft_inv")}
     launches = sum(sum(c["launches"] for c in p.values()) for p in prof)
-    value = a.steps * ws / (total_ms / 1e3)
+    value = whole_job_rate(a.steps, ws, total_ms)
     if a.only_timed:
         if rank == 0:
             print(json.dumps({"value": value, "unit": UNIT, "ms_per_step": total_ms / a.steps,
@@ -280,7 +300,7 @@ def run_ours(a):
     for i, b in enumerate(W["betas"]):
         if a.fp64_budget_s <= 0 or time.perf_counter() - t_start > a.fp64_budget_s:
             break
-        G64, _ = make(b, 0, 1000 * rank + i)
+        G64, _ = make(b, 0, replica_seeds(rank, i + 1)[i])
         x64.zero_()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)

@@ -140,7 +140,13 @@ __device__ __forceinline__ cpx<T> q2_diag(const T* __restrict__ tab, int n2, int
   return r;
 }
 
-// Q1 scalar operator at node (ix, iy) of a grid with n1 nodes per side.
+// Q1 scalar operator at node (ix, iy) of a grid with n1 nodes per side:
+// a (M1 x M1) + b (K1 x M1 + M1 x K1) + 2c (W1 x X1 - X1 x W1), evaluated
+// separably.  The stiffness part uses that every row of the 1-D stiffness
+// band sums to zero (Neumann rows included): sum_k K1_ik x_k =
+// sum_k K1_ik (x_k - x_i).  The differences of neighbouring values are exact
+// for smooth fields, so the near-null (nearly constant) component that the
+// corner-pinned pressure Laplacian barely damps causes no cancellation.
 template <class T, bool CONV>
 __device__ __forceinline__ cpx<T> q1_op(const T* __restrict__ tab, int n1, int ix, int iy,
                                         const cpx<T>* __restrict__ x, cpx<T> a, T b, T c) {
@@ -152,30 +158,39 @@ __device__ __forceinline__ cpx<T> q1_op(const T* __restrict__ tab, int n1, int i
   const T* Xx = tab + (size_t)(3 * n1 + ix) * 3;
   const T* Wy = tab + (size_t)(2 * n1 + iy) * 3;
   const T* Xy = tab + (size_t)(3 * n1 + iy) * 3;
+  cpx<T> v[3][3];
+#pragma unroll
+  for (int dy = 0; dy < 3; ++dy) {
+    const cpx<T>* row = x + (size_t)clampi(iy + dy - 1, 0, n1 - 1) * n1;
+#pragma unroll
+    for (int dx = 0; dx < 3; ++dx) v[dy][dx] = row[clampi(ix + dx - 1, 0, n1 - 1)];
+  }
   cpx<T> accM = czero<T>(), accK = czero<T>(), accN = czero<T>();
 #pragma unroll
   for (int dy = 0; dy < 3; ++dy) {
-    const int jy = clampi(iy + dy - 1, 0, n1 - 1);
-    const cpx<T>* row = x + (size_t)jy * n1;
     cpx<T> sM = czero<T>(), sK = czero<T>(), sW = czero<T>(), sX = czero<T>();
 #pragma unroll
     for (int dx = 0; dx < 3; ++dx) {
-      const int jx = clampi(ix + dx - 1, 0, n1 - 1);
-      const cpx<T> v = row[jx];
-      rfma(sM, Mx[dx], v);
-      rfma(sK, Kx[dx], v);
+      rfma(sM, Mx[dx], v[dy][dx]);
+      rfma(sK, Kx[dx], v[dy][dx] - v[dy][1]);
       if (CONV) {
-        rfma(sW, Wx[dx], v);
-        rfma(sX, Xx[dx], v);
+        rfma(sW, Wx[dx], v[dy][dx]);
+        rfma(sX, Xx[dx], v[dy][dx]);
       }
     }
     rfma(accM, My[dy], sM);
     rfma(accK, My[dy], sK);
-    rfma(accK, Ky[dy], sM);
     if (CONV) {
       rfma(accN, Xy[dy], sW);
       rfma(accN, -Wy[dy], sX);
     }
+  }
+#pragma unroll
+  for (int dx = 0; dx < 3; ++dx) {
+    cpx<T> tK = czero<T>();
+#pragma unroll
+    for (int dy = 0; dy < 3; ++dy) rfma(tK, Ky[dy], v[dy][dx] - v[1][dx]);
+    rfma(accK, Mx[dx], tK);
   }
   cpx<T> r = a * accM;
   rfma(r, b, accK);

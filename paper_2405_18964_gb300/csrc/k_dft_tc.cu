@@ -10,7 +10,10 @@
 // bulk asynchronous copies (cp.async.bulk) per reduction chunk of TC_KC.
 // One elected thread issues tcgen05.mma for every kept piece product and
 // commits to an mbarrier per pipeline stage; two stages overlap the next
-// chunk's loads with the current chunk's MMAs.  The epilogue reads the
+// chunk's loads with the current chunk's MMAs.  The leading (hi x hi)
+// products accumulate in D1 (TMEM columns 0..255) and the correction
+// products in D2 (columns 256..511), summed in the epilogue: the large sum
+// then takes one FP32 accumulation per MMA step instead of one per product.  The epilogue reads the
 // accumulator with tcgen05.ld (warp w reads TMEM lanes 32 (w mod 4) + lane,
 // i.e. one spatial slot per thread) and writes coalesced rows of the output.
 //
@@ -33,6 +36,7 @@ constexpr int TC_KC = 32;           // reduction elements per pipeline chunk
 constexpr int TC_THREADS = 256;
 constexpr int TC_STAGES = 2;
 constexpr uint32_t TC_TMEM_COLS = 512;
+constexpr uint32_t TC_D2 = 256;     // column of the second accumulator
 constexpr unsigned long long TC_WAIT_NS = 1000000000ull;  // 1 s of global time
 
 template <int S>
@@ -145,6 +149,27 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
 // 16 consecutive 32-bit accumulator columns of this thread's TMEM lane
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v);
+// Columns col .. col+15 of the accumulator at column `base`, reading no column
+// at or beyond base + limit (the block is shifted back and realigned; values
+// past the limit come back as 0).  col is warp-uniform.
+__device__ __forceinline__ void tmem_ld16_lim(uint32_t tl, uint32_t base, int col, int limit, float* v) {
+  if (col + 16 <= limit) {
+    tmem_ld16(tl + base + (uint32_t)col, v);
+    return;
+  }
+  const int cs = limit - 16, shift = col - cs;
+  float t[16];
+  tmem_ld16(tl + base + (uint32_t)cs, t);
+#pragma unroll
+  for (int q = 0; q < 16; ++q) {
+    float val = 0.f;
+#pragma unroll
+    for (int s2 = 0; s2 < 16; ++s2)
+      if (s2 == shift && q + s2 < 16) val = t[q + s2];
+    v[q] = val;
+  }
+}
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
   uint32_t r[16];
   asm volatile(
@@ -322,7 +347,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) dft_tc_kernel(TcArgs a) {
           for (int t = 0; t < STEPS; ++t) {
             const uint64_t ad = smem_desc(abase + (uint32_t)(Sc::pa(p) * APB) + 256u * t, LBO, SBO);
             const uint64_t bd = smem_desc(bbase + (uint32_t)(Sc::pb(p) * bpb) + 256u * t, LBO, SBO);
-            mma<S>(tmem, ad, bd, idesc, (ch > 0 || p > 0 || t > 0) ? 1u : 0u);
+            // leading product (hi x hi) into D1 (columns 0..), the smaller
+            // correction products into D2 (columns 256..): the FP32 sums of
+            // the large terms then take one accumulation per MMA step only
+            if (p == 0)
+              mma<S>(tmem, ad, bd, idesc, (ch > 0 || t > 0) ? 1u : 0u);
+            else
+              mma<S>(tmem + TC_D2, ad, bd, idesc, (ch > 0 || p > 1 || t > 0) ? 1u : 0u);
           }
         mma_commit(mbar0 + 8 * s);
         ++cm[s];
@@ -342,13 +373,20 @@ __global__ void __launch_bounds__(TC_THREADS, 1) dft_tc_kernel(TcArgs a) {
     const int lg = warp & 3, grp = warp >> 2;
     const uint32_t tl = tmem + ((uint32_t)(32 * lg) << 16);
     const long long i = tile * TC_M + 32 * lg + lane;
-    float re[16], im[16];
+    float re[16], im[16], c2[16];
+    constexpr int LIM = (int)TC_D2;  // columns per accumulator
     if (DIR == 0) {
       const int Jh = (a.J + 1) / 2;
       const int j0 = grp * Jh, j1 = min(a.J, j0 + Jh);
       for (int jb = j0; jb < j1; jb += 16) {
-        tmem_ld16(tl + (uint32_t)jb, re);
-        tmem_ld16(tl + (uint32_t)(a.J - 1 + jb), im);
+        tmem_ld16_lim(tl, 0, jb, LIM, re);
+        tmem_ld16_lim(tl, TC_D2, jb, LIM, c2);
+#pragma unroll
+        for (int q = 0; q < 16; ++q) re[q] += c2[q];
+        tmem_ld16_lim(tl, 0, a.J - 1 + jb, LIM, im);
+        tmem_ld16_lim(tl, TC_D2, a.J - 1 + jb, LIM, c2);
+#pragma unroll
+        for (int q = 0; q < 16; ++q) im[q] += c2[q];
         if (i < a.nblk)
 #pragma unroll
           for (int q = 0; q < 16; ++q) {
@@ -363,11 +401,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) dft_tc_kernel(TcArgs a) {
       const int Kh = (a.K + 1) / 2;
       const int k0 = grp * Kh, k1 = min(a.K, k0 + Kh);
       for (int kb = k0; kb < k1; kb += 16) {
-        tmem_ld16(tl + (uint32_t)kb, re);
+        tmem_ld16_lim(tl, 0, kb, LIM, re);
+        tmem_ld16_lim(tl, TC_D2, kb, LIM, c2);
         if (i < a.nblk)
 #pragma unroll
           for (int q = 0; q < 16; ++q)
-            if (kb + q < k1) a.y[(size_t)(kb + q) * a.nblk + i] = (double)re[q];
+            if (kb + q < k1) a.y[(size_t)(kb + q) * a.nblk + i] = (double)re[q] + (double)c2[q];
       }
     }
     tc_fence_before();

@@ -65,3 +65,48 @@ def freq_blocks(P, Xh):
     """GPU frequency vector [J][nblk] -> list of oracle (v, lam, p, mu) vectors."""
     Xh = np.asarray(Xh).reshape(-1, layout.block_len(P))
     return [layout.to_oracle_freq(P, Xh[j]) for j in range(Xh.shape[0])]
+
+
+def _gmres_fp32_vectors(A, Pinv, s, tol, maxit, fixed_its=0):
+    """The oracle's inner GMRES with every Krylov vector rounded to FP32
+    (operator and preconditioner stay exact FP64): fixed iteration count."""
+    Amul = (lambda v: A @ v) if not callable(A) else A
+    r32 = lambda v: v.astype(np.complex64).astype(np.complex128)
+    m = fixed_its
+    s = r32(s.astype(complex))
+    beta0 = np.linalg.norm(s)
+    if beta0 == 0:
+        return np.zeros(len(s), complex), 0
+    V = np.zeros((m + 1, len(s)), complex)
+    Z = np.zeros((m, len(s)), complex)
+    H = np.zeros((m + 1, m), complex)
+    V[0] = r32(s / beta0)
+    for i in range(m):
+        Z[i] = r32(Pinv(V[i]))
+        w = r32(Amul(Z[i]))
+        for l in range(i + 1):
+            H[l, i] = np.vdot(V[l], w)
+            w = r32(w - H[l, i] * V[l])
+        H[i + 1, i] = np.linalg.norm(w)
+        V[i + 1] = r32(w / H[i + 1, i])
+    g = np.zeros(m + 1, complex)
+    g[0] = beta0
+    y = np.linalg.lstsq(H, g, rcond=None)[0]
+    return Z.T @ y, m
+
+
+def fp32_arnoldi_solves(P, s, freqs, blocks, fixed_its):
+    """Oracle frequency-block solves with FP32-rounded inner Krylov vectors.
+
+    The FP32 sensitivity of the inner GMRES itself differs strongly between
+    frequencies (at 64 x 64, n_t = 256 it is ~30x larger at j = K/4 than at
+    j = 0): comparisons of FP32 block solves at full size are held to a bar
+    derived from this emulation (reading R23)."""
+    from oracle import inexact
+    saved = inexact.gmres
+    inexact.gmres = _gmres_fp32_vectors
+    try:
+        pc = inexact.PinTPreconditioner(P, s, fixed_inner_its=fixed_its)
+        return {j: pc.solve_block(j, blocks[j]) for j in freqs}
+    finally:
+        inexact.gmres = saved

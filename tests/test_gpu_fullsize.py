@@ -11,8 +11,13 @@ final solution, recomputed row by row from the oracle's Kronecker form).
 import numpy as np
 import pytest
 
-from gpu_pairs import (FP32_TOL, FP64_TOL, KP_FP64_TOL, freq_blocks, make_pair, part_errors, relerr, settings_of,
-                       to_dev)
+from gpu_pairs import (FP32_TOL, FP64_TOL, KP_FP64_TOL, fp32_arnoldi_solves, freq_blocks, make_pair, part_errors,
+                       relerr, settings_of, to_dev)
+
+# FP32 bar at full size (reading R23): 10x the change of the oracle's own
+# result when only its inner Krylov vectors are rounded to FP32, at least the
+# FP32 apply bar 1e-5.
+FP32_EMULATION_FACTOR = 10.0
 from oracle import inexact, layout
 from paper_2405_18964_gb300 import inputs
 
@@ -101,10 +106,12 @@ def test_frequency_block_solves_full_size(prec):
     pc = inexact.PinTPreconditioner(P, settings_of(G), fixed_inner_its=3)
     got = freq_blocks(P, yh.cpu().numpy())
     rs = freq_blocks(P, rh)
+    emu = fp32_arnoldi_solves(P, settings_of(G), SAMPLED_J, rs, 3) if prec else {}
     for j in SAMPLED_J:
         ref = pc.solve_block(j, rs[j])
         if prec:
-            assert relerr(got[j], ref) <= FP32_TOL, j
+            bar = max(FP32_TOL, FP32_EMULATION_FACTOR * relerr(emu[j], ref))
+            assert relerr(got[j], ref) <= bar, (j, relerr(got[j], ref), bar)
         else:
             # pressure through the K_p multigrid: evaluation-order bar (see gpu_pairs)
             e = part_errors(P, got[j], ref)
@@ -193,18 +200,24 @@ def test_preconditioner_apply_full_size(prec):
     z = torch.zeros(G.kkt_len, dtype=torch.float64, device="cuda")
     G.apply_preconditioner(to_dev(r.ravel()), z)
     pc = inexact.PinTPreconditioner(P, settings_of(G), fixed_inner_its=3)
-    Y = np.zeros_like(F)
-    for j in freqs:
-        y = layout.from_oracle_freq(P, pc.solve_block(j, layout.to_oracle_freq(P, F[j])))
-        Y[j] = y
-        if 0 < j < K // 2:
-            Y[K - j] = np.conj(y)
-    zo = np.fft.ifft(Y, axis=0).real
+    blocks = {j: layout.to_oracle_freq(P, F[j]) for j in freqs}
+
+    def to_time(sol):
+        Y = np.zeros_like(F)
+        for j in freqs:
+            y = layout.from_oracle_freq(P, sol[j])
+            Y[j] = y
+            if 0 < j < K // 2:
+                Y[K - j] = np.conj(y)
+        return np.fft.ifft(Y, axis=0).real
+
+    zo = to_time({j: pc.solve_block(j, blocks[j]) for j in freqs})
     got = z.cpu().numpy().reshape(K, -1)
     err = relerr(got, zo)
     print(f"apply full size prec {prec}: relerr {err:.3e}")
     if prec:
-        assert err <= FP32_TOL
+        emu = relerr(to_time(fp32_arnoldi_solves(P, settings_of(G), freqs, blocks, 3)), zo)
+        assert err <= max(FP32_TOL, FP32_EMULATION_FACTOR * emu), (err, emu)
     else:
         # the pressure values pass through the K_p multigrid (reading R21)
         s = layout.slots(P)

@@ -270,3 +270,18 @@ def test_pressure_multigrid_rounding_spread():
     # the two evaluations are the same operator: they agree far beyond FP32,
     # and differ by more than the generic FP64 bar of 1e-12
     assert 5e-13 < spread < 4e-12, spread
+
+
+def test_fp32_krylov_emulation_is_fp32_level():
+    """The FP32-Krylov emulation that sets the full-size FP32 bars (reading
+    R23) changes a frequency-block solve at FP32 level: above FP64 rounding,
+    far below the inner tolerance."""
+    from gpu_pairs import fp32_arnoldi_solves
+    from oracle import layout
+    P = kkt.Problem("stokes", 3, 8, 1 / 9, 1e-3, 1e-2, 0.0, 1.0, None)
+    s = inexact.Settings()
+    g = {1: layout.to_oracle_freq(P, np.random.default_rng(4).standard_normal(layout.block_len(P)) + 0j)}
+    exact = inexact.PinTPreconditioner(P, s, fixed_inner_its=3).solve_block(1, g[1])
+    emu = fp32_arnoldi_solves(P, s, [1], g, 3)[1]
+    d = np.abs(emu - exact).max() / np.abs(exact).max()
+    assert 1e-10 < d < 1e-5, d

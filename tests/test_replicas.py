@@ -1,0 +1,54 @@
+"""Multi-GPU runs are replicas (no collective on the data path): the host
+logic of bench.py under two gloo ranks on the CPU — max-over-ranks timing,
+the whole-job rate, distinct data per replica, and the reference arm that
+runs on rank 0 only."""
+import os
+import socket
+import subprocess
+import sys
+
+import pytest
+
+torch = pytest.importorskip("torch")
+import torch.distributed as tdist  # noqa: E402
+import torch.multiprocessing as mp  # noqa: E402
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, world, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    import bench
+    r, ws, dist = bench.dist_init(backend="gloo")
+    assert (r, ws) == (rank, world)
+    ms = 100.0 + 50.0 * rank                      # the slower rank decides
+    t = bench.max_over_ranks(ms, dist, device="cpu")
+    out[rank] = (t, bench.whole_job_rate(3, ws, t), tuple(bench.replica_seeds(rank, 3)))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_time_and_seed_as_replicas():
+    world, port = 2, _free_port()
+    with mp.Manager() as m:
+        out = m.dict()
+        mp.spawn(_rank_main, args=(world, port, out), nprocs=world, join=True)
+        res = dict(out)
+    assert res[0][0] == res[1][0] == 150.0
+    assert res[0][1] == pytest.approx(3 * 2 / 0.15)
+    assert set(res[0][2]).isdisjoint(res[1][2])
+
+
+def test_reference_arm_runs_on_rank_zero_only():
+    env = dict(os.environ, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1")
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                        "--warmup", "3"], env=env, capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0 and r.stdout.strip() == ""
+    assert not tdist.is_initialized()
