@@ -133,6 +133,10 @@ typedef struct {
   size_t device_bytes;        /* workspace owned by the handle              */
 } pint_sizes;
 
+/* Upper estimate of the device memory pint_create would allocate for p
+ * (bytes; 0 for invalid parameters).  Computed on the host, no CUDA call. */
+size_t pint_estimate_device_bytes(const pint_params* p);
+
 /* Defaults from Sec. 5: FGMRES(30), inner tolerance 1e-2, 4 V-cycles with
  * 2+2 SOR sweeps (omega = 1), 10 Chebyshev steps, 6 Uzawa steps, mu = 3/4,
  * inner cap 100, outer tolerance 1e-8.  Problem fields are set to a Stokes
@@ -258,6 +262,51 @@ typedef struct {
 pint_status pint_profile_enable(pint_handle h, unsigned mask);
 /* Synchronise the handle's stream and copy the counters out. */
 pint_status pint_profile_read(pint_handle h, pint_profile* out);
+
+/* ------------------------------------------------------------------------
+ * Serving loop: continuous batching of control problems.
+ *
+ * A server owns max_active worker slots on the current device.  Requests
+ * (any kind, level, n_t, beta, nu, precision) wait in submission order; a
+ * free slot admits the oldest waiting request as soon as its estimate
+ * pint_estimate_device_bytes(p) fits in what the requests on the GPU leave
+ * of the server's budget.  Each admitted request gets its own handle and
+ * CUDA stream: data and Krylov state stay resident on the device until it
+ * completes, and the kernels of all admitted requests run concurrently.  A
+ * request whose handle cannot be created for lack of memory returns to the
+ * head of the queue until a running request completes, and fails with
+ * PINT_ERR_OOM only on an otherwise idle server.  Results are identical to
+ * a solve of the same request alone (the kernels are deterministic).
+ * ---------------------------------------------------------------------- */
+typedef struct pint_server_s* pint_server;
+
+typedef struct {
+  size_t device_budget; /* bytes admitted requests may hold; 0: 90% of free memory */
+  int max_active;       /* worker slots (requests on the GPU at once), 1..64      */
+} pint_server_params;
+
+typedef struct {
+  long long submitted, completed, failed, active, queued;
+  size_t budget_bytes, bytes_in_use, bytes_peak; /* by estimate               */
+  int active_peak;                               /* most requests at once     */
+} pint_server_stats;
+
+/* Start the worker threads.  PINT_ERR_ARG for max_active outside [1, 64]. */
+pint_status pint_server_create(const pint_server_params* sp, pint_server* out);
+/* Queue a request.  vd (host, [n_t][2][n_s]) is copied, as are the optional
+ * f ([n_t][2][n_s]) and v0 ([2][n_s]).  PINT_ERR_ARG for invalid params,
+ * PINT_ERR_OOM if the estimate exceeds the whole budget. */
+pint_status pint_server_submit(pint_server s, const pint_params* p, const double* vd, const double* f,
+                               const double* v0, long long* id);
+/* Block until request id completes; copy its solution (host, kkt_len
+ * doubles, may be null), info and latency (submission to completion, ms).
+ * Returns the request's solve status.  Each id is collected once. */
+pint_status pint_server_wait(pint_server s, long long id, double* x_host, pint_solve_info* info, double* latency_ms);
+pint_status pint_server_get_stats(pint_server s, pint_server_stats* out);
+/* Finish every queued and running request, then stop the workers. */
+pint_status pint_server_destroy(pint_server s);
+/* Message of the last failed server call of the calling thread. */
+const char* pint_server_last_error(void);
 
 /* Failure injection for tests (no GPU fault is involved).
  * PINT_INJECT_DFT_STALL: the next tensor-core DFT launch of the handle arms

@@ -61,6 +61,16 @@ class Profile(ctypes.Structure):
 
 _lib = None
 _P = ctypes.c_void_p
+class ServerParams(ctypes.Structure):
+    _fields_ = [("device_budget", ctypes.c_size_t), ("max_active", ctypes.c_int)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_longlong), ("completed", ctypes.c_longlong), ("failed", ctypes.c_longlong),
+                ("active", ctypes.c_longlong), ("queued", ctypes.c_longlong), ("budget_bytes", ctypes.c_size_t),
+                ("bytes_in_use", ctypes.c_size_t), ("bytes_peak", ctypes.c_size_t), ("active_peak", ctypes.c_int)]
+
+
 _SIGS = {
     "pint_default_params": (None, [ctypes.POINTER(Params)]),
     "pint_create": (ctypes.c_int, [ctypes.POINTER(Params), _P, ctypes.POINTER(_P)]),
@@ -81,6 +91,14 @@ _SIGS = {
     "pint_profile_enable": (ctypes.c_int, [_P, ctypes.c_uint]),
     "pint_profile_read": (ctypes.c_int, [_P, ctypes.POINTER(Profile)]),
     "pint_debug_inject": (ctypes.c_int, [_P, ctypes.c_int]),
+    "pint_estimate_device_bytes": (ctypes.c_size_t, [ctypes.POINTER(Params)]),
+    "pint_server_create": (ctypes.c_int, [ctypes.POINTER(ServerParams), ctypes.POINTER(_P)]),
+    "pint_server_submit": (ctypes.c_int, [_P, ctypes.POINTER(Params), _P, _P, _P, ctypes.POINTER(ctypes.c_longlong)]),
+    "pint_server_wait": (ctypes.c_int, [_P, ctypes.c_longlong, _P, ctypes.POINTER(SolveInfo),
+                                        ctypes.POINTER(ctypes.c_double)]),
+    "pint_server_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(ServerStats)]),
+    "pint_server_destroy": (ctypes.c_int, [_P]),
+    "pint_server_last_error": (ctypes.c_char_p, []),
     "pint_last_error": (ctypes.c_char_p, [_P]),
 }
 
@@ -265,3 +283,59 @@ class Problem:
     def component_apply(self, which, j, x, y):
         w = COMPONENT[which] if isinstance(which, str) else int(which)
         _check(lib().pint_component_apply(self.h, w, j, _dptr(x, "complex128"), _dptr(y, "complex128")), self.h)
+
+
+def estimate_device_bytes(params):
+    """Upper estimate of the device memory a handle for these parameters holds."""
+    return int(lib().pint_estimate_device_bytes(ctypes.byref(params)))
+
+
+class Server:
+    """Serving loop (pint_server_*): continuous batching of control problems
+    on the current device; see include/pint.h."""
+
+    def __init__(self, max_active=4, device_budget=0):
+        sp = ServerParams(device_budget, max_active)
+        h = ctypes.c_void_p()
+        code = lib().pint_server_create(ctypes.byref(sp), ctypes.byref(h))
+        if code != 0:
+            raise PintError(code, lib().pint_server_last_error().decode())
+        self.h = h
+
+    def submit(self, params, vd, f=None, v0=None):
+        """Queue a request (host arrays are copied); returns its id."""
+        n_s = (2 * (1 << params.level) + 1) ** 2
+        keep = [np.ascontiguousarray(vd, dtype=np.float64).reshape(params.n_t * 2 * n_s)]
+        ptrs = [keep[0].ctypes.data_as(ctypes.c_void_p)]
+        for a, n in ((f, params.n_t * 2 * n_s), (v0, 2 * n_s)):
+            if a is None:
+                ptrs.append(None)
+            else:
+                keep.append(np.ascontiguousarray(a, dtype=np.float64).reshape(n))
+                ptrs.append(keep[-1].ctypes.data_as(ctypes.c_void_p))
+        rid = ctypes.c_longlong()
+        code = lib().pint_server_submit(self.h, ctypes.byref(params), ptrs[0], ptrs[1], ptrs[2], ctypes.byref(rid))
+        if code != 0:
+            raise PintError(code, lib().pint_server_last_error().decode())
+        return rid.value
+
+    def wait(self, rid, kkt_len, check=True):
+        """Block until request rid completes: (x, info, latency_ms, status)."""
+        x = np.zeros(kkt_len)
+        info = SolveInfo()
+        lat = ctypes.c_double()
+        code = lib().pint_server_wait(self.h, rid, x.ctypes.data_as(ctypes.c_void_p), ctypes.byref(info),
+                                      ctypes.byref(lat))
+        if check and code != 0:
+            raise PintError(code, lib().pint_server_last_error().decode())
+        return x, info, lat.value, code
+
+    def stats(self):
+        st = ServerStats()
+        lib().pint_server_get_stats(self.h, ctypes.byref(st))
+        return {f: getattr(st, f) for f, _ in ServerStats._fields_}
+
+    def close(self):
+        if self.h:
+            lib().pint_server_destroy(self.h)
+            self.h = None

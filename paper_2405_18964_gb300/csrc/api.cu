@@ -1108,6 +1108,31 @@ void pint_default_params(pint_params* p) {
   p->dft_mode = PINT_DFT_AUTO;
 }
 
+size_t pint_estimate_device_bytes(const pint_params* p) {
+  std::string why;
+  if (!valid_params(p, why)) return 0;
+  const long long N = 1LL << p->level, K = p->n_t, J = K / 2 + 1;
+  const long long ns = (2 * N + 1) * (2 * N + 1), nq = (N + 1) * (N + 1), nblk = 4 * ns + 2 * nq;
+  const bool fp32 = p->prec == PINT_PREC_FP32, oseen = p->kind == PINT_OSEEN;
+  const long long cs = fp32 ? 8 : 16;  // bytes per complex value of the preconditioner
+  const long long m = p->outer_restart;
+  const long long m_in = p->fixed_inner_its > 0 ? p->fixed_inner_its : p->inner_maxit;
+  long long b = 0;
+  b += (2 * m + 4) * K * nblk * 8 + J * nblk * 16;  // outer FGMRES basis, b, x, t; FP64 frequency staging
+  b += 5 * J * nblk * cs;                            // frequency vectors
+  if (!p->linear) b += (2 * m_in + 1) * J * nblk * cs + (long long)J * (m_in + 1) * m_in * 16 * 2;
+  const MGLayout l2 = make_layout(p->level, (int)N, 2), l1 = make_layout(p->level, (int)N, 1);
+  const long long mgq2 = oseen ? 2 * J : 4 * J, mgq1 = 2 * J, chq2 = oseen ? 2 * J : 2, chq1 = 2 * J;
+  b += std::max(mgq2 * l2.per_job, mgq1 * l1.per_job) * cs;
+  b += std::max(chq2 * 2 * ns, chq1 * 2 * nq) * cs;
+  if (p->wind == PINT_WIND_RECIRC)
+    for (int l = 0; l < p->level; ++l) {
+      const long long n2 = 2 * (N >> l) + 1, w6 = (n2 + 5) / 6;
+      b += 36 * w6 * w6 * 25 * (fp32 ? 4 : 8) + nq * 9 * 8;
+    }
+  return (size_t)(b + b / 20 + (64LL << 20));  // 5% + 64 MiB for tables and small state
+}
+
 pint_status pint_create(const pint_params* p, void* stream, pint_handle* out) {
   if (!out) {
     g_err = "null output handle";

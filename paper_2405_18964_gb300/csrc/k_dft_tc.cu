@@ -519,13 +519,13 @@ void dft_tc_build_table(int K, int scheme, bool inverse, unsigned char* out) {
 namespace {
 template <int S, int DIR>
 void launch_tc(const DftTc& d, const TcArgs& a, cudaStream_t st) {
-  static int nsm = 0;
-  if (!nsm) {
-    int dev = 0;
+  // SM count of the device, queried once (thread-safe initialisation)
+  static const int nsm = [] {
+    int dev = 0, v = 0;
     cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    if (nsm <= 0) nsm = 1;
-  }
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    return v > 0 ? v : 1;
+  }();
   const size_t stage = a_piece_bytes<S>() * Scheme<S>::NP + d.chunk_bytes;
   size_t smem = TC_STAGES * stage + 2 * TC_STAGES * 8 + 16;
   // at least 116 KB so that one CTA (and one 512-column TMEM allocation) fits per SM

@@ -674,13 +674,13 @@ __global__ void __launch_bounds__(1024, 1) mg_q2b_kernel(MGLaunch<T> L) {
 // fewer jobs than SMs each job gets more threads (the kernels are compiled
 // for a 64-register budget, valid for every size used here).
 int cta_threads(int njobs) {
-  static int nsm = 0;
-  if (!nsm) {
-    int dev = 0;
+  // SM count of the device, queried once (thread-safe initialisation)
+  static const int nsm = [] {
+    int dev = 0, v = 0;
     cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    if (nsm <= 0) nsm = 1;
-  }
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    return v > 0 ? v : 1;
+  }();
   if (njobs <= nsm) return 1024;
   if (njobs <= 2 * nsm) return 512;
   return MG_THREADS;
