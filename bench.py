@@ -37,6 +37,11 @@ WORKLOADS = {
     "stokes64_nt32": dict(kind=0, level=6, K=32, T=1.0, betas=[1e-4], nu=1e-2, x0=0.0, x1=1.0, wind=0),
     # small case the oracle solves in seconds (8x8 grid, n_t = 8)
     "stokes8_nt8": dict(kind=0, level=3, K=8, T=1.0, betas=[1e-2], nu=1e-2, x0=0.0, x1=1.0, wind=0),
+    # Oseen control, 128x128 Q2-Q1 on [-1,1]^2, n_t = 128, nu = 1/100, recirculating wind
+    "oseen128_nt128": dict(kind=1, level=7, K=128, T=1.0, betas=[1e-4], nu=1e-2, x0=-1.0, x1=1.0, wind=1),
+    # large Oseen control, 256x256, n_t = 128, nu = 1/500, beta = 1e-6, FGMRES(20)
+    "oseen256_nt128": dict(kind=1, level=8, K=128, T=1.0, betas=[1e-6], nu=2e-3, x0=-1.0, x1=1.0, wind=1,
+                           restart=20),
 }
 # FGMRES iterations per solve measured on the GB300 (FP64 and FP32 preconditioner
 # agree) for the middle beta of each workload; used to extrapolate the oracle's
@@ -52,7 +57,14 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="stokes64_nt256", choices=list(WORKLOADS))
+    ap.add_argument("--workload", default="stokes64_nt256", choices=list(WORKLOADS) + ["serve"],
+                    help="'serve': the serving stream (pint_server_*), see --requests/--rate")
+    ap.add_argument("--requests", type=int, default=16, help="serve: number of requests in the stream")
+    ap.add_argument("--rate", type=float, default=1.0, help="serve: Poisson arrival rate (requests/s)")
+    ap.add_argument("--slots", type=int, default=8, help="serve: worker slots of the server")
+    ap.add_argument("--serve-prec", type=int, default=1, choices=[0, 1], help="serve: 1 = FP32 preconditioner")
+    ap.add_argument("--max-level", type=int, default=7, help="serve: largest grid level drawn (7 = 128x128)")
+    ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--fp64-budget-s", type=float, default=20.0,
                     help="wall-clock budget for the FP64-plain comparison solves")
     ap.add_argument("--cpu-sample-s", type=float, default=20.0)
@@ -63,7 +75,7 @@ def parse():
                     help="run the warm-up and timed solves only (for profiler captures)")
     ap.add_argument("--beta", type=float, default=None,
                     help="solve for this one beta only (profiler captures: one handle on the device)")
-    ap.add_argument("--outer-restart", type=int, default=30,
+    ap.add_argument("--outer-restart", type=int, default=None,
                     help="FGMRES restart length; smaller values shrink the device footprint for profiler "
                          "captures (the reported metric uses 30)")
     return ap.parse_args()
@@ -227,7 +239,7 @@ def run_ours(a):
     def make(beta, prec, seed):
         p = binding.default_params(kind=W["kind"], level=W["level"], n_t=K, tau=tau, beta=beta, nu=W["nu"],
                                    x0=W["x0"], x1=W["x1"], wind=W["wind"], prec=prec, inner_maxit=a.inner_maxit,
-                                   outer_restart=a.outer_restart)
+                                   outer_restart=a.outer_restart or W.get("restart", 30))
         G = binding.Problem(p, stream=stream.cuda_stream)
         vd = inputs.desired_state(N, W["x0"], W["x1"], K, tau, T, seed)
         G.set_data(vd)
@@ -277,6 +289,7 @@ def run_ours(a):
             print(json.dumps({"value": value, "unit": UNIT, "ms_per_step": total_ms / a.steps,
                               "gpu_launches": int(launches),
                               "mg_q2_avg_launch_ms": mg["ms"] / max(1, mg["timed"]),
+                              "autotune": binding.autotune_report().strip().splitlines(),
                               "dft_avg_ms": {d: c["ms"] / max(1, c["timed"]) for d, c in dft.items()}}), flush=True)
         return
 
@@ -349,8 +362,8 @@ def run_ours(a):
         "warmup": a.warmup, "ms_per_step": round(total_ms / a.steps, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32 preconditioner / f64 FGMRES",
         "data": "synthetic (seeded curl of 4 random sine modes)",
-        "config": {"workload": a.workload, "kind": "stokes", "grid": f"{N}x{N} Q2-Q1", "n_t": K, "T": T,
-                   "betas": W["betas"], "nu": W["nu"], "outer": "FGMRES(30), tol 1e-8", "inner_tol": 1e-2,
+        "config": {"workload": a.workload, "kind": "oseen" if W["kind"] else "stokes", "grid": f"{N}x{N} Q2-Q1", "n_t": K, "T": T,
+                   "betas": W["betas"], "nu": W["nu"], "outer": f"FGMRES({W.get('restart', 30)}), tol 1e-8", "inner_tol": 1e-2,
                    "l2": "inputs larger than L2 (FP64 FGMRES basis 9.4 GB)", "parallelism": f"replicas x{ws}"},
         "latency_ms": {"p50": round(float(np.percentile(lat, 50)), 3), "p99": round(float(np.percentile(lat, 99)), 3)},
         "outer_iterations": [inf.outer_iterations for inf in infos],
@@ -369,6 +382,7 @@ def run_ours(a):
                      "avg_launch_ms": round(avg_ms, 4), "timed_launches": mg["timed"],
                      "algorithmic_bytes_per_launch": alg},
         "dft": dft_line,
+        "autotune": binding.autotune_report().strip().splitlines(),
         "clocks": clocks,
     }
     if rank == 0 and not a.no_cpu_baseline:
@@ -379,6 +393,80 @@ def run_ours(a):
         G.close()
     if dist:
         dist.destroy_process_group()
+
+
+# --------------------------------------------------------- serving stream
+def serve_requests(seed, count, max_level):
+    """The serving stream's requests, drawn from default_rng(seed) in this
+    order per request: kind 50/50; N in {16, 32, 64, 128} (levels 4..7, capped
+    at max_level; Oseen requests drawn at 16x16 run at 32x32); n_t in
+    {16, 32, 64, 128, 256}; log10 beta ~ U[-6, -2]; nu in {1/50, 1/100} for
+    Oseen (1e-2 for Stokes); a data seed."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(count):
+        oseen = bool(rng.integers(0, 2))
+        level = int(rng.choice([4, 5, 6, 7]))
+        K = int(rng.choice([16, 32, 64, 128, 256]))
+        beta = float(10.0 ** rng.uniform(-6.0, -2.0))
+        nu = float(rng.choice([1 / 50, 1 / 100])) if oseen else 1e-2
+        dseed = int(rng.integers(0, 2 ** 31))
+        if oseen:
+            level = max(level, 5)  # 16x16 Oseen: the inner solver stagnates (reading R24)
+        out.append(dict(oseen=oseen, level=min(level, max_level), K=K, beta=beta, nu=nu, seed=dseed))
+    return out
+
+
+def run_serve(a):
+    """Serving stream through pint_server_*: Poisson arrivals, continuous
+    admission by device memory; throughput and latency percentiles."""
+    import torch
+    from paper_2405_18964_gb300 import binding, inputs
+    reqs = serve_requests(a.seed, a.requests, a.max_level)
+    arr = np.cumsum(np.random.default_rng(a.seed + 1).exponential(1.0 / a.rate, size=len(reqs)))
+    built = []
+    for r in reqs:
+        x0, x1 = (-1.0, 1.0) if r["oseen"] else (0.0, 1.0)
+        tau = 1.0 / (r["K"] + 1)
+        p = binding.default_params(kind=int(r["oseen"]), level=r["level"], n_t=r["K"], tau=tau, beta=r["beta"],
+                                   nu=r["nu"], x0=x0, x1=x1, wind=int(r["oseen"]), prec=a.serve_prec)
+        vd = inputs.desired_state(2 ** r["level"], x0, x1, r["K"], tau, 1.0, seed=r["seed"])
+        n = r["K"] * (4 * (2 ** (r["level"] + 1) + 1) ** 2 + 2 * (2 ** r["level"] + 1) ** 2)
+        built.append((p, vd, n))
+    torch.cuda.synchronize()
+    srv = binding.Server(max_active=a.slots)
+    clk = Clocks(0)
+    clk.start()
+    t0 = time.perf_counter()
+    ids = []
+    for (p, vd, _), ta in zip(built, arr):
+        dt = ta - (time.perf_counter() - t0)
+        if dt > 0:
+            time.sleep(dt)
+        ids.append(srv.submit(p, vd))
+    lat, its, fails = [], [], 0
+    for rid, (_, _, n) in zip(ids, built):
+        _, info, ms, code = srv.wait(rid, n, check=False)
+        lat.append(ms)
+        its.append(info.outer_iterations)
+        fails += code != 0
+    wall = time.perf_counter() - t0
+    clocks = clk.stop()
+    st = srv.stats()
+    srv.close()
+    line = {"metric": "serving stream: solves/s and p50/p99 latency (FP32 precond)" if a.serve_prec else
+            "serving stream: solves/s and p50/p99 latency (FP64 precond)",
+            "value": round(len(ids) / wall, 4), "unit": "solves/s", "n_gpus": 1, "higher_is_better": True,
+            "latency_ms": {"p50": round(float(np.percentile(lat, 50)), 1),
+                           "p99": round(float(np.percentile(lat, 99)), 1)},
+            "requests": len(ids), "failed": fails, "arrival_rate": a.rate, "slots": a.slots,
+            "active_peak": st["active_peak"], "bytes_peak": st["bytes_peak"], "budget_bytes": st["budget_bytes"],
+            "outer_iterations": its, "wall_s": round(wall, 2),
+            "config": {"workload": "serve", "seed": a.seed, "max_level": a.max_level,
+                       "requests": [{k: (round(v, 8) if isinstance(v, float) else v) for k, v in r.items()}
+                                    for r in reqs]},
+            "data": "synthetic (seeded)", "clocks": clocks}
+    print(json.dumps(line), flush=True)
 
 
 # --------------------------------------------------------- oracle timing
@@ -441,7 +529,7 @@ def run_reference(a):
         pc.solve_block(1 + i % (K // 2), g)
         per.append(time.perf_counter() - s0)
     dt = time.perf_counter() - t0
-    outer_its = OUTER_ITS_MEASURED[a.workload]
+    outer_its = OUTER_ITS_MEASURED.get(a.workload, 25)
     est = outer_its * K * (dt / a.steps)
     cores = len(os.sched_getaffinity(0))
     v = 1.0 / est
@@ -459,7 +547,7 @@ def run_reference(a):
 
 def main():
     a = parse()
-    if not a.only_timed and (a.beta is not None or a.outer_restart != 30):
+    if not a.only_timed and (a.beta is not None or a.outer_restart is not None):
         sys.exit("--beta and --outer-restart change the workload: use them with --only-timed only")
     if a.impl == "reference":
         run_reference(a)
@@ -468,6 +556,9 @@ def main():
     if not os.path.exists(binding.LIB_PATH):
         import __graft_entry__
         __graft_entry__.build()
+    if a.workload == "serve":
+        run_serve(a)
+        return
     run_ours(a)
 
 

@@ -308,6 +308,19 @@ pint_status pint_server_destroy(pint_server s);
 /* Message of the last failed server call of the calling thread. */
 const char* pint_server_last_error(void);
 
+/* Autotuner of the multigrid launches (on by default, process-wide): for
+ * each launch shape (space, grid, number of fields, precision, operator
+ * variant) three launches after the first three (untimed: module loading,
+ * first touch of the workspaces) run with 256, 512 and 1024 threads per
+ * CTA, timed by CUDA events on the launch stream; later launches use the
+ * fastest.  Results do not depend on the choice.  pint_autotune(0) restores
+ * the fixed heuristic (1024 threads up to one field per SM, 512 up to two,
+ * else 256). */
+void pint_autotune(int on);
+/* The tuner's decisions as text, one launch shape per line, written to buf
+ * (NUL-terminated, truncated to len); returns the size needed. */
+size_t pint_autotune_report(char* buf, size_t len);
+
 /* Failure injection for tests (no GPU fault is involved).
  * PINT_INJECT_DFT_STALL: the next tensor-core DFT launch of the handle arms
  * its first pipeline barrier for 16 bytes more than its bulk copy delivers,

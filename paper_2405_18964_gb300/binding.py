@@ -92,6 +92,8 @@ _SIGS = {
     "pint_profile_read": (ctypes.c_int, [_P, ctypes.POINTER(Profile)]),
     "pint_debug_inject": (ctypes.c_int, [_P, ctypes.c_int]),
     "pint_estimate_device_bytes": (ctypes.c_size_t, [ctypes.POINTER(Params)]),
+    "pint_autotune": (None, [ctypes.c_int]),
+    "pint_autotune_report": (ctypes.c_size_t, [ctypes.c_char_p, ctypes.c_size_t]),
     "pint_server_create": (ctypes.c_int, [ctypes.POINTER(ServerParams), ctypes.POINTER(_P)]),
     "pint_server_submit": (ctypes.c_int, [_P, ctypes.POINTER(Params), _P, _P, _P, ctypes.POINTER(ctypes.c_longlong)]),
     "pint_server_wait": (ctypes.c_int, [_P, ctypes.c_longlong, _P, ctypes.POINTER(SolveInfo),
@@ -283,6 +285,19 @@ class Problem:
     def component_apply(self, which, j, x, y):
         w = COMPONENT[which] if isinstance(which, str) else int(which)
         _check(lib().pint_component_apply(self.h, w, j, _dptr(x, "complex128"), _dptr(y, "complex128")), self.h)
+
+
+def autotune(on=True):
+    """Switch the multigrid CTA-size autotuner on or off (process-wide)."""
+    lib().pint_autotune(1 if on else 0)
+
+
+def autotune_report():
+    """The autotuner's decisions, one launch shape per line."""
+    n = lib().pint_autotune_report(None, 0)
+    buf = ctypes.create_string_buffer(n)
+    lib().pint_autotune_report(buf, n)
+    return buf.value.decode()
 
 
 def estimate_device_bytes(params):

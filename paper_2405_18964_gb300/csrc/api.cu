@@ -1477,6 +1477,18 @@ pint_status pint_component_apply(pint_handle h, int which, int j, const double* 
                  : component_T<double>(h, h->e64, which, j, in, out);
 }
 
+void pint_autotune(int on) { mg_autotune_enable(on != 0); }
+
+size_t pint_autotune_report(char* buf, size_t len) {
+  const std::string r = mg_autotune_report();
+  if (buf && len) {
+    const size_t n = std::min(len - 1, r.size());
+    memcpy(buf, r.data(), n);
+    buf[n] = 0;
+  }
+  return r.size() + 1;
+}
+
 pint_status pint_debug_inject(pint_handle h, int what) {
   if (!h) return g_err = "null handle", PINT_ERR_ARG;
   if (what != PINT_INJECT_DFT_STALL) return h->fail(PINT_ERR_ARG, "unknown injection code");

@@ -17,11 +17,19 @@
 //    V-cycles.
 // One CTA owns one field (job) for the whole solve, so a batched MG
 // application over all frequencies and components is one launch.
+#include <atomic>
+#include <cstdio>
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
+
 #include "kernels.h"
 
 namespace pint {
 
 constexpr int MG_THREADS = 256;
+
 
 // ----------------------------------------------------------------------------
 // Stencil weights.  On the uniform grid the 2-D weights of a constant-
@@ -104,6 +112,44 @@ __device__ __forceinline__ cpx<T> stencil(const cpx<T>* __restrict__ w, const T*
   return acc;
 }
 
+// Q1 (A x) at a node from the precombined weights in difference form:
+// sum_{k != c} w_k (x_k - x_c) + rs x_c, rs = a * (row sum of the mass
+// stencil); the stiffness rows sum to zero exactly (Neumann rows included),
+// so the near-constant mode of the pinned pressure Laplacian cancels in the
+// exact differences of neighbouring values instead of in rounded sums.
+template <class T>
+__device__ __forceinline__ cpx<T> stencil_q1d(const cpx<T>* __restrict__ w, T rs, int n, int ix, int iy,
+                                              const cpx<T>* __restrict__ x) {
+  const cpx<T> xc = x[(size_t)iy * n + ix];
+  cpx<T> acc = rs * xc;
+#pragma unroll
+  for (int dy = 0; dy < 3; ++dy) {
+    const cpx<T>* row = x + (size_t)clampi(iy + dy - 1, 0, n - 1) * n;
+#pragma unroll
+    for (int dx = 0; dx < 3; ++dx) {
+      if (dx == 1 && dy == 1) continue;
+      rfma(acc, w[dy * 3 + dx].x, row[clampi(ix + dx - 1, 0, n - 1)] - xc);
+    }
+  }
+  return acc;
+}
+
+// Row sums of a M on Q1 level l per node type (FP64 -> T): the mass part
+// only, the stiffness rows summing to zero.
+template <class T>
+__device__ void level_rowsums_q1(const Tabs<double>& t64, int l, int n, double a, T* srs) {
+  const double* tab = t64.q1[l];
+  for (int type = threadIdx.x; type < 9; type += blockDim.x) {
+    const int ix = type_rep<1>(type % 3, n), iy = type_rep<1>(type / 3, n);
+    double sx = 0.0, sy = 0.0;
+    for (int d = 0; d < 3; ++d) {
+      sx += tab[(size_t)ix * 3 + d];
+      sy += tab[(size_t)iy * 3 + d];
+    }
+    srs[type] = T(a * sx * sy);
+  }
+}
+
 template <int SP>
 __device__ __forceinline__ bool is_unknown(int ix, int iy, int n) {
   if (SP == 2) return ix > 0 && iy > 0 && ix < n - 1 && iy < n - 1;
@@ -116,8 +162,7 @@ __device__ __forceinline__ bool is_unknown(int ix, int iy, int n) {
 // one weight set.  Q1: colours (ix mod 2, iy mod 2), pinned corner skipped.
 template <class T, int SP, bool CONV, bool CW>
 __device__ void sor_colour(int n, cpx<T>* const* X, const cpx<T>* const* B, int nf, const cpx<T>* sw,
-                           const cpx<T>* sdi, const T* n2d, T c, int colour, T omega, const T* q1tab = nullptr,
-                           cpx<T> ca = cpx<T>{}, T cb = T(0)) {
+                           const cpx<T>* sdi, const T* n2d, T c, int colour, T omega, const T* srs = nullptr) {
   if (SP == 2) {
     const int cx = colour % 3, cy = colour / 3;
     for (int sub = 0; sub < 4; ++sub) {
@@ -149,11 +194,9 @@ __device__ void sor_colour(int n, cpx<T>* const* X, const cpx<T>* const* B, int 
       if ((ix | iy) == 0) continue;
       const size_t id = (size_t)iy * n + ix;
       cpx<T>* x = X[f];
-      // separable evaluation from the 1-D bands: the pinned Laplacian's
-      // near-constant mode needs exactly zero row sums of K_p
-      const cpx<T> ax = q1_op<T, false>(q1tab, n, ix, iy, x, ca, cb, T(0));
-      const cpx<T> dg = q1_diag<T, false>(q1tab, n, ix, iy, ca, cb, T(0));
-      x[id] = x[id] + omega * cdiv(B[f][id] - ax, dg);
+      const int type = node_type<1>(ix, iy, n);
+      const cpx<T> ax = stencil_q1d<T>(sw + type * 9, srs[type], n, ix, iy, x);
+      x[id] = x[id] + omega * sdi[type].x * (B[f][id] - ax);
     }
   }
 }
@@ -191,6 +234,7 @@ template <class T, int SP, bool CONV, bool CW>
 __global__ void __launch_bounds__(1024, 1) mg_kernel(MGLaunch<T> L) {
   __shared__ cpx<T> sw[100];
   __shared__ cpx<T> sdi[9];
+  __shared__ T srs[9];
   __shared__ cpx<T>* Xs[PINT_MAXLEV][PINT_MAXF];
   __shared__ const cpx<T>* Bs[PINT_MAXLEV][PINT_MAXF];
   __shared__ cpx<T>* Rs[PINT_MAXLEV][PINT_MAXF];
@@ -229,18 +273,21 @@ __global__ void __launch_bounds__(1024, 1) mg_kernel(MGLaunch<T> L) {
       const int n = L.lay.n[l];
       const T* n2d = CONV ? L.n2d[l] : nullptr;
       level_weights<T, SP>(L.t64, l, n, a, bb, sw, sdi);
+      if (SP == 1) level_rowsums_q1<T>(L.t64, l, n, a.x, srs);
       __syncthreads();
       constexpr int NCOL = SP == 2 ? 9 : 4;
       for (int s = 0; s < L.pre; ++s)
         for (int col = 0; col < NCOL; ++col) {
-          sor_colour<T, SP, CONV, CW>(n, Xs[l], Bs[l], nf, sw, sdi, n2d, cc, col, omega, L.tabs.q1[l], ca, cbT);
+          sor_colour<T, SP, CONV, CW>(n, Xs[l], Bs[l], nf, sw, sdi, n2d, cc, col, omega, srs);
           __syncthreads();
         }
       for (int q = threadIdx.x; q < nf * n * n; q += blockDim.x) {
         const int f = q / (n * n), i = q % (n * n);
         const int ix = i % n, iy = i / n;
         cpx<T> r = czero<T>();
-        if (is_unknown<SP>(ix, iy, n)) r = Bs[l][f][i] - q1_op<T, false>(L.tabs.q1[l], n, ix, iy, Xs[l][f], ca, cbT, T(0));
+        if (is_unknown<SP>(ix, iy, n))
+          r = Bs[l][f][i] - stencil_q1d<T>(sw + node_type<1>(ix, iy, n) * 9, srs[node_type<1>(ix, iy, n)], n, ix,
+                                           iy, Xs[l][f]);
         Rs[l][f][i] = r;
       }
       __syncthreads();
@@ -315,6 +362,7 @@ __global__ void __launch_bounds__(1024, 1) mg_kernel(MGLaunch<T> L) {
       const int nc = L.lay.n[l + 1];
       const T* n2d = CONV ? L.n2d[l] : nullptr;
       level_weights<T, SP>(L.t64, l, n, a, bb, sw, sdi);
+      if (SP == 1) level_rowsums_q1<T>(L.t64, l, n, a.x, srs);
       for (int q = threadIdx.x; q < nf * n * n; q += blockDim.x) {
         const int f = q / (n * n), i = q % (n * n);
         const int ix = i % n, iy = i / n;
@@ -354,7 +402,7 @@ __global__ void __launch_bounds__(1024, 1) mg_kernel(MGLaunch<T> L) {
       constexpr int NCOL = SP == 2 ? 9 : 4;
       for (int s = 0; s < L.post; ++s)
         for (int col = NCOL - 1; col >= 0; --col) {
-          sor_colour<T, SP, CONV, CW>(n, Xs[l], Bs[l], nf, sw, sdi, n2d, cc, col, omega, L.tabs.q1[l], ca, cbT);
+          sor_colour<T, SP, CONV, CW>(n, Xs[l], Bs[l], nf, sw, sdi, n2d, cc, col, omega, srs);
           __syncthreads();
         }
     }
@@ -448,9 +496,9 @@ template <class T, bool CONV, bool CW>
 __device__ __forceinline__ void sor_node_b(int n, const BLay& b, int ccx, int ccy, int q, int& id, int& type,
                                            int& rx, int& ry, bool& valid) {
   const int sub = q / b.s, i = q - sub * b.s;
+  const int my = udiv(i, b.mg), mx = i - my * b.w6;
   rx = ccx + 3 * (sub & 1);
   ry = ccy + 3 * (sub >> 1);
-  const int my = udiv(i, b.mg), mx = i - my * b.w6;
   const int ix = 6 * mx + rx, iy = 6 * my + ry;
   valid = q < 4 * b.s && ix >= 1 && iy >= 1 && ix <= n - 2 && iy <= n - 2;
   type = (rx & 1) + 2 * (ry & 1);
@@ -543,14 +591,15 @@ __global__ void __launch_bounds__(1024, 1) mg_q2b_kernel(MGLaunch<T> L) {
       cpx<T>* R = Rl(l);
       for (int q = threadIdx.x; q < 36 * b.s; q += blockDim.x) {
         const int cls = q / b.s, i = q - cls * b.s;
-        const int rx = cls % 6, ry = cls / 6;
         const int my = udiv(i, b.mg), mx = i - my * b.w6;
+        const int id = q;
+        const int rx = cls % 6, ry = cls / 6;
         const int ix = 6 * mx + rx, iy = 6 * my + ry;
         cpx<T> r = czero<T>();
         if (ix >= 1 && iy >= 1 && ix <= n - 2 && iy <= n - 2)
-          r = B[q] - stencil_b<T, CONV, CW>(sw + ((rx & 1) + 2 * (ry & 1)) * 25, b,
-                                            CONV ? n2d + (size_t)q * 25 : nullptr, cc, rx, ry, q, X);
-        R[q] = r;
+          r = B[id] - stencil_b<T, CONV, CW>(sw + ((rx & 1) + 2 * (ry & 1)) * 25, b,
+                                             CONV ? n2d + (size_t)id * 25 : nullptr, cc, rx, ry, id, X);
+        R[id] = r;
       }
       __syncthreads();
       // restriction R = P^T onto the coarse level, coarse iterate zeroed
@@ -686,10 +735,102 @@ int cta_threads(int njobs) {
   return MG_THREADS;
 }
 
+// ---------------------------------------------------------------------------
+// Autotuner of the multigrid CTA size.  For each launch shape (space, finest
+// nodes per side, job count, precision, operator variant) three launches
+// after a short warm-up try 256, 512 and 1024 threads per CTA, timed by CUDA
+// events on the launch stream, and every later launch of that shape uses the
+// fastest.  The choice
+// does not change the results: every node's update is the same arithmetic
+// whichever thread performs it, and the nodes of a colour are independent.
+// ---------------------------------------------------------------------------
+namespace {
+constexpr int TUNE_CAND[3] = {256, 512, 1024};
+constexpr int TUNE_WARMUP = 3;  // launches of a shape before timing (module loading, first touch)
+struct MgTune {
+  int seen = 0;
+  int best = -1;      // index into TUNE_CAND once decided
+  int next = 0;   // next candidate to time
+  float ms[3] = {-1.f, -1.f, -1.f};
+  cudaEvent_t a[3] = {}, b[3] = {};
+};
+using MgKey = std::tuple<int, int, int, int, int>;  // space, n0, njobs, sizeof(T), variant
+std::mutex g_tune_mu;
+std::map<MgKey, MgTune> g_tune;
+std::atomic<bool> g_tune_on{true};
+
+// Threads for this launch; slot >= 0 means "time this launch into slot".
+int tune_pick(const MgKey& key, int fallback, int& slot, cudaEvent_t& ea, cudaEvent_t& eb) {
+  slot = -1;
+  if (!g_tune_on.load()) return fallback;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  MgTune& t = g_tune[key];
+  if (t.seen < TUNE_WARMUP) {
+    ++t.seen;
+    return fallback;
+  }
+  if (t.best < 0) {
+    bool all = true;
+    for (int i = 0; i < 3; ++i) {
+      if (t.ms[i] < 0.f && i < t.next) {
+        const cudaError_t q = cudaEventQuery(t.b[i]);
+        if (q == cudaSuccess)
+          cudaEventElapsedTime(&t.ms[i], t.a[i], t.b[i]);
+        else if (q == cudaErrorNotReady && cudaPeekAtLastError() == cudaErrorNotReady)
+          cudaGetLastError();  // "not ready" is not an error of any launch
+      }
+      all = all && t.ms[i] >= 0.f;
+    }
+    if (all) {
+      t.best = 0;
+      for (int i = 1; i < 3; ++i)
+        if (t.ms[i] < t.ms[t.best]) t.best = i;
+      for (int i = 0; i < 3; ++i) {
+        cudaEventDestroy(t.a[i]);
+        cudaEventDestroy(t.b[i]);
+      }
+    } else if (t.next < 3) {
+      slot = t.next++;
+      cudaEventCreate(&t.a[slot]);
+      cudaEventCreate(&t.b[slot]);
+      ea = t.a[slot];
+      eb = t.b[slot];
+      return TUNE_CAND[slot];
+    } else {
+      return fallback;  // a timing is still in flight
+    }
+  }
+  return TUNE_CAND[t.best];
+}
+}  // namespace
+
+void mg_autotune_enable(bool on) { g_tune_on.store(on); }
+
+std::string mg_autotune_report() {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  std::string out;
+  char line[256];
+  for (const auto& kv : g_tune) {
+    const auto& k = kv.first;
+    const MgTune& t = kv.second;
+    snprintf(line, sizeof line, "space=%d n=%d jobs=%d %s variant=%d: 256:%.3f 512:%.3f 1024:%.3f ms -> %d\n",
+             std::get<0>(k), std::get<1>(k), std::get<2>(k), std::get<3>(k) == 4 ? "fp32" : "fp64",
+             std::get<4>(k), t.ms[0], t.ms[1], t.ms[2], t.best >= 0 ? TUNE_CAND[t.best] : 0);
+    out += line;
+  }
+  return out;
+}
+
 template <class T>
 void launch_mg(const MGLaunch<T>& L, cudaStream_t st) {
   if (L.njobs <= 0) return;
-  dim3 grid(L.njobs), block(cta_threads(L.njobs));
+  const int variant = L.conv ? 2 : (L.cw ? 1 : 0);
+  int slot = -1;
+  cudaEvent_t ea = nullptr, eb = nullptr;
+  const int threads = tune_pick(MgKey(L.space, L.lay.n[0], L.njobs, (int)sizeof(T), variant), cta_threads(L.njobs),
+                                slot, ea, eb);
+  dim3 grid(L.njobs), block(threads);
+  if (slot >= 0) cudaEventRecord(ea, st);
   if (L.space == 2) {
     // one velocity field per CTA, class-blocked layout in the workspace
     if (L.conv)
@@ -701,6 +842,7 @@ void launch_mg(const MGLaunch<T>& L, cudaStream_t st) {
   } else {
     mg_kernel<T, 1, false, false><<<grid, block, 0, st>>>(L);
   }
+  if (slot >= 0) cudaEventRecord(eb, st);
 }
 
 // ---------------------------------------------------------------------------

@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
 #include "common.cuh"
 
 namespace pint {
@@ -56,6 +58,9 @@ struct MGLaunch {
 
 template <class T>
 void launch_mg(const MGLaunch<T>& L, cudaStream_t st);
+// CTA-size autotuner of launch_mg (on by default) and its decisions as text.
+void mg_autotune_enable(bool on);
+std::string mg_autotune_report();
 
 template <class T>
 struct ChebLaunch {
