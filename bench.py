@@ -400,8 +400,8 @@ def serve_requests(seed, count, max_level):
     """The serving stream's requests, drawn from default_rng(seed) in this
     order per request: kind 50/50; N in {16, 32, 64, 128} (levels 4..7, capped
     at max_level; Oseen requests drawn at 16x16 run at 32x32); n_t in
-    {16, 32, 64, 128, 256}; log10 beta ~ U[-6, -2]; nu in {1/50, 1/100} for
-    Oseen (1e-2 for Stokes); a data seed."""
+    {16, 32, 64, 128, 256}; log10 beta ~ U[-6, -2] (capped at 1e-4 for
+    Oseen); nu in {1/50, 1/100} for Oseen (1e-2 for Stokes); a data seed."""
     rng = np.random.default_rng(seed)
     out = []
     for _ in range(count):
@@ -412,7 +412,8 @@ def serve_requests(seed, count, max_level):
         nu = float(rng.choice([1 / 50, 1 / 100])) if oseen else 1e-2
         dseed = int(rng.integers(0, 2 ** 31))
         if oseen:
-            level = max(level, 5)  # 16x16 Oseen: the inner solver stagnates (reading R24)
+            level = max(level, 5)    # 16x16 Oseen: the inner solver stagnates (reading R24)
+            beta = min(beta, 1e-4)   # larger beta: the Q_j multigrid diverges (reading R25)
         out.append(dict(oseen=oseen, level=min(level, max_level), K=K, beta=beta, nu=nu, seed=dseed))
     return out
 

@@ -56,7 +56,7 @@ typedef enum {
   PINT_ERR_OOM = 2,            /* device or host allocation failed         */
   PINT_ERR_CUDA = 3,           /* a CUDA call failed (message has details) */
   PINT_ERR_NOT_CONVERGED = 4,  /* outer solve hit outer_maxit             */
-  PINT_ERR_NONFINITE = 5,      /* NaN/Inf in host input data              */
+  PINT_ERR_NONFINITE = 5,      /* NaN/Inf in host input data or in a Krylov vector */
   PINT_ERR_TIMEOUT = 6,        /* a bounded device wait gave up            */
   PINT_ERR_STATE = 7           /* call out of order (e.g. solve before set_data) */
 } pint_status;

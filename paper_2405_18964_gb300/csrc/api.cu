@@ -1012,6 +1012,14 @@ pint_status fgmres(pint_ctx* c, double* x, pint_solve_info* info) {
       cudaMemcpyAsync(c->h_pinned, c->oh, sizeof(double) * (2 * (i + 1) + 1), cudaMemcpyDeviceToHost, st);
       if (!c->cu(cudaStreamSynchronize(st), "FGMRES iteration")) return PINT_ERR_CUDA;
       c->drain();
+      for (int l = 0; l <= 2 * (i + 1); ++l)
+        if (!std::isfinite(c->h_pinned[l])) {
+          inf.outer_iterations = total;
+          inf.relres = NAN;
+          if (info) *info = inf;
+          return c->fail(PINT_ERR_NONFINITE, "non-finite value in the preconditioned Krylov vector (iteration " +
+                                                 std::to_string(total + 1) + ")");
+        }
       const double hn = std::sqrt(std::max(0.0, c->h_pinned[2 * (i + 1)]));
       for (int l = 0; l <= i; ++l) H[(size_t)l * m + i] = c->h_pinned[l] + c->h_pinned[i + 1 + l];
       H[(size_t)(i + 1) * m + i] = hn;
