@@ -63,6 +63,12 @@ struct Engine {
 
   const T* n2d[PINT_MAXLEV] = {};  // per-level Q2 convection stencils (conv only)
   const T* np2d = nullptr;         // finest-level Q1 convection stencils (conv only)
+  int active_freqs = 0;            // frequencies still active in the inner solve (0: all / unknown)
+  int active_jobs(int njobs, const int* active) const {
+    return active && active_freqs > 0 && active_freqs < c_J() ? std::max(1, (int)((long long)njobs * active_freqs / c_J()))
+                                                              : 0;
+  }
+  int c_J() const;
   void mg(int space, bool conv, const FieldJob* jobs, int njobs, cpx<T>* xb, const cpx<T>* bb, const int* active,
           int fields_per_job = 2);
   void cheb(int space, const FieldJob* jobs, int njobs, cpx<T>* xb, const cpx<T>* bb, const int* active,
@@ -189,6 +195,11 @@ struct pint_ctx {
   bool launched(const char* what) { return cu(cudaGetLastError(), what); }
 };
 
+template <class T>
+int Engine<T>::c_J() const {
+  return c->J;
+}
+
 // RAII scope around the launches of one kernel class: counts nk kernels and,
 // if the class is being timed, records a CUDA event pair on the stream.
 struct Prof {
@@ -255,6 +266,7 @@ void Engine<T>::mg(int space, bool conv, const FieldJob* jobs, int njobs, cpx<T>
   L.omega = c->p.sor_omega;
   L.space = space;
   L.conv = conv;
+  L.active_jobs = active_jobs(njobs, active);
   PROF(c, space == 2 ? PINT_PROF_MG_Q2 : PINT_PROF_MG_Q1, 1);
   launch_mg<T>(L, c->st);
 }
@@ -277,6 +289,7 @@ void Engine<T>::cheb(int space, const FieldJob* jobs, int njobs, cpx<T>* xb, con
   L.lmin = space == 2 ? Q2_LMIN : Q1_LMIN;
   L.lmax = space == 2 ? Q2_LMAX : Q1_LMAX;
   L.space = space;
+  L.active_jobs = active_jobs(njobs, active);
   PROF(c, PINT_PROF_CHEB, 1);
   launch_cheb<T>(L, c->st);
 }
@@ -431,10 +444,12 @@ void Engine<T>::inner_solve(const cpx<T>* S, cpx<T>* X, int* its_host) {
     launch_gmres_start(G, st);
     launch_bscale_inv<T>(J, nb, S, V, nb, G.beta0, 1, G.active, st);
   }
+  active_freqs = 0;
   for (int i = 0; i < m; ++i) {
     cpx<T>* Vi = V + (size_t)i * vs;
     cpx<T>* Zi = Z + (size_t)i * vs;
     cpx<T>* Vn = V + (size_t)(i + 1) * vs;
+    if (i > 0) active_freqs = *c->h_count;  // still-active frequencies after the previous step
     block_prec(Vi, Zi, G.active);
     block_matvec(c->d_blkZ, Zi, Vn, G.active);
     // classical Gram-Schmidt with one reorthogonalisation (CGS2) against
@@ -456,6 +471,7 @@ void Engine<T>::inner_solve(const cpx<T>* S, cpx<T>* X, int* its_host) {
     c->drain();
     if (*c->h_count == 0) break;
   }
+  active_freqs = 0;
   {
     PROF(c, PINT_PROF_INNER, 2);
     launch_gmres_finish<T>(G, nb, Z, (long long)vs, X, st);

@@ -827,8 +827,12 @@ void launch_mg(const MGLaunch<T>& L, cudaStream_t st) {
   const int variant = L.conv ? 2 : (L.cw ? 1 : 0);
   int slot = -1;
   cudaEvent_t ea = nullptr, eb = nullptr;
-  const int threads = tune_pick(MgKey(L.space, L.lay.n[0], L.njobs, (int)sizeof(T), variant), cta_threads(L.njobs),
-                                slot, ea, eb);
+  // When only some frequencies are still active (late inner iterations), the
+  // few live fields get larger CTAs; otherwise the tuned size for this shape.
+  const bool tail = L.active_jobs > 0 && L.active_jobs < L.njobs;
+  const int threads = tail ? cta_threads(L.active_jobs)
+                           : tune_pick(MgKey(L.space, L.lay.n[0], L.njobs, (int)sizeof(T), variant),
+                                       cta_threads(L.njobs), slot, ea, eb);
   dim3 grid(L.njobs), block(threads);
   if (slot >= 0) cudaEventRecord(ea, st);
   if (L.space == 2) {
@@ -923,7 +927,7 @@ __global__ void __launch_bounds__(1024, 1) cheb_kernel(ChebLaunch<T> L) {
 template <class T>
 void launch_cheb(const ChebLaunch<T>& L, cudaStream_t st) {
   if (L.njobs <= 0) return;
-  const int thr = cta_threads(L.njobs);
+  const int thr = cta_threads(L.active_jobs > 0 && L.active_jobs < L.njobs ? L.active_jobs : L.njobs);
   if (L.space == 2)
     cheb_kernel<T, 2><<<L.njobs, thr, 0, st>>>(L);
   else

@@ -52,6 +52,7 @@ struct MGLaunch {
   double omega;
   int space;  // 2 = Q2 (velocity component), 1 = Q1 (pressure)
   bool conv;
+  int active_jobs;  // > 0: jobs whose frequency is still active (sizes the CTAs), 0: all
 };
 
 #define PINT_NC_MAX 9
@@ -77,6 +78,7 @@ struct ChebLaunch {
   int steps;
   double lmin, lmax;
   int space;
+  int active_jobs;  // > 0: jobs whose frequency is still active (sizes the CTAs), 0: all
 };
 
 template <class T>

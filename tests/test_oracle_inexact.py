@@ -285,3 +285,58 @@ def test_fp32_krylov_emulation_is_fp32_level():
     emu = fp32_arnoldi_solves(P, s, [1], g, 3)[1]
     d = np.abs(emu - exact).max() / np.abs(exact).max()
     assert 1e-10 < d < 1e-5, d
+
+
+def _hat_preconditioned_operator(P, schur):
+    """Dense matrix of P_C^{-1} A for the block preconditioner diag(W_j, W_j,
+    S_j, S_j) of Z_j (Sec. 3.2) inside the FFT diagonalisation:
+    schur='exact' uses S_j = B W_j^{-1} B^T (P^_C, Theorem 2), schur='commutator'
+    the approximation S^_j (P~_C, Theorem 3)."""
+    import scipy.linalg as sla
+    blocks = {}
+    for j in range(P.K):
+        _, _, _, c1, c2 = inexact.stokes_constants(P, j)
+        W = ((1 + c1) * P.Ms + c2 * P.Ls).toarray()
+        Wv = sla.block_diag(W, W)
+        B = P.Bv.toarray()
+        if schur == "exact":
+            S = B @ np.linalg.solve(Wv, B.T)
+        else:
+            Kp, Mp = P.Kpr.toarray(), P.Mpr.toarray()
+            S = np.linalg.inv((1 + c1) * np.linalg.inv(Kp) + P.nu * c2 * np.linalg.inv(Mp))
+        Pj = sla.block_diag(Wv, Wv, S, S)
+        Tl, Tr = inexact.T_matrices(P, j)
+        blocks[j] = np.linalg.inv(Tl.toarray() @ Pj @ Tr.toarray())
+
+    def solver(j, rhs):
+        return P.g_to_ylam(blocks[j] @ P.ylam_to_g(rhs))
+
+    A = P.kkt_matrix().toarray()
+    return np.column_stack([P.pc_inverse(A[:, k], solver)[0] for k in range(A.shape[1])])
+
+
+@pytest.mark.parametrize("schur", ["exact", "commutator"])
+def test_theorems_2_3_eigenvalue_clusters(schur):
+    """Theorems 2 and 3: at most 4 n_v eigenvalues of P^_C^{-1} A (P~_C^{-1} A)
+    lie outside |mu| in [a, b], with [a, b] = [1/sqrt(12), (1+sqrt(5))/2] for
+    the exact Schur complement (Eq. SchurComplementHatBounds) and [a c, b d]
+    for the commutator one, [c, d] bounding |lambda(S^_j^{-1} B W_j^{-1} B^T)|
+    over the frequencies (the lemma before Theorem 3)."""
+    P = kkt.Problem("stokes", 2, 4, 1 / 5, 1e-2, 1e-2, 0.0, 1.0, None)
+    a, b = 1 / np.sqrt(12), (1 + np.sqrt(5)) / 2
+    if schur == "commutator":
+        cs, ds = [], []
+        for j in range(P.K):
+            _, _, _, c1, c2 = inexact.stokes_constants(P, j)
+            W = ((1 + c1) * P.Ms + c2 * P.Ls).toarray()
+            import scipy.linalg as sla
+            B = P.Bv.toarray()
+            S = B @ np.linalg.solve(sla.block_diag(W, W), B.T)
+            Shat_inv = (1 + c1) * np.linalg.inv(P.Kpr.toarray()) + P.nu * c2 * np.linalg.inv(P.Mpr.toarray())
+            ev = np.abs(np.linalg.eigvals(Shat_inv @ S))
+            cs.append(ev.min())
+            ds.append(ev.max())
+        a, b = a * min(cs), b * max(ds)
+    mu = np.abs(np.linalg.eigvals(_hat_preconditioned_operator(P, schur)))
+    inside = np.count_nonzero((mu >= a * (1 - 1e-9)) & (mu <= b * (1 + 1e-9)))
+    assert inside >= len(mu) - 4 * P.nv, (inside, len(mu), P.nv)
