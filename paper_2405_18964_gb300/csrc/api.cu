@@ -57,6 +57,7 @@ struct Engine {
   cpx<T>* V = nullptr;  // inner GMRES basis [m+1][J][nblk]
   cpx<T>* Z = nullptr;  // [m][J][nblk]
   cpx<T>* mgws = nullptr;
+  cpx<T>* mgws_q1 = nullptr;  // pressure multigrid workspace when it runs beside the velocity one
   cpx<T>* chebws = nullptr;
   T* cosk = nullptr;
   T* sink = nullptr;
@@ -70,9 +71,9 @@ struct Engine {
   }
   int c_J() const;
   void mg(int space, bool conv, const FieldJob* jobs, int njobs, cpx<T>* xb, const cpx<T>* bb, const int* active,
-          int fields_per_job = 2);
+          int fields_per_job = 2, cudaStream_t stream = nullptr, cpx<T>* ws = nullptr);
   void cheb(int space, const FieldJob* jobs, int njobs, cpx<T>* xb, const cpx<T>* bb, const int* active,
-            int fields_per_job = 2);
+            int fields_per_job = 2, cudaStream_t stream = nullptr);
   void block_prec(const cpx<T>* U, cpx<T>* Out, const int* active);
   void block_matvec(const BlkCoef* coef, const cpx<T>* X, cpx<T>* Out, const int* active);
   void inner_solve(const cpx<T>* S, cpx<T>* X, int* its_host);
@@ -112,6 +113,8 @@ struct pint_ctx {
   int* d_active_one = nullptr;
   GmresState gs{};
   DftTc tc{};              // tensor-core time DFT (FP32 preconditioner), scheme 0 = off
+  cudaStream_t st_aux = nullptr;                  // second stream of the Stokes block preconditioner
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int* h_tcerr = nullptr;  // pinned copy of tc.err
 
   // outer FGMRES (FP64)
@@ -205,21 +208,23 @@ int Engine<T>::c_J() const {
 struct Prof {
   pint_ctx* c;
   int cls;
+  cudaStream_t s;
   cudaEvent_t a = nullptr;
-  Prof(pint_ctx* c_, int cls_, int nk) : c(c_), cls(cls_) {
+  Prof(pint_ctx* c_, int cls_, int nk, cudaStream_t s_ = nullptr) : c(c_), cls(cls_), s(s_ ? s_ : c_->st) {
     c->prof_launch[cls] += nk;
     if ((c->prof_mask >> cls) & 1u) {
       a = c->take_event();
-      cudaEventRecord(a, c->st);
+      cudaEventRecord(a, s);
     }
   }
   ~Prof() {
     if (!a) return;
     cudaEvent_t b = c->take_event();
-    cudaEventRecord(b, c->st);
+    cudaEventRecord(b, s);
     c->pend.push_back({cls, a, b});
     if (c->pend.size() > 8192) {
       cudaStreamSynchronize(c->st);
+      if (c->st_aux) cudaStreamSynchronize(c->st_aux);
       c->drain();
     }
   }
@@ -227,6 +232,7 @@ struct Prof {
 #define PROF_CAT2(a, b) a##b
 #define PROF_CAT(a, b) PROF_CAT2(a, b)
 #define PROF(ctx, cls, nk) Prof PROF_CAT(prof_scope_, __LINE__)((ctx), (cls), (nk))
+#define PROF_ON(ctx, cls, nk, stream) Prof PROF_CAT(prof_scope_, __LINE__)((ctx), (cls), (nk), (stream))
 
 // ============================================================================
 // Engine<T>
@@ -244,7 +250,7 @@ Tabs<float>& tabs_of<float>(pint_ctx* c) {
 
 template <class T>
 void Engine<T>::mg(int space, bool conv, const FieldJob* jobs, int njobs, cpx<T>* xb, const cpx<T>* bb,
-                   const int* active, int fields_per_job) {
+                   const int* active, int fields_per_job, cudaStream_t stream, cpx<T>* ws) {
   MGLaunch<T> L{};
   L.tabs = tabs;
   L.t64 = c->t64;
@@ -258,7 +264,7 @@ void Engine<T>::mg(int space, bool conv, const FieldJob* jobs, int njobs, cpx<T>
   L.njobs = njobs;
   L.xbase = xb;
   L.bbase = bb;
-  L.ws = mgws;
+  L.ws = ws ? ws : mgws;
   L.active = active;
   L.cycles = c->p.mg_cycles;
   L.pre = c->p.mg_pre;
@@ -267,13 +273,14 @@ void Engine<T>::mg(int space, bool conv, const FieldJob* jobs, int njobs, cpx<T>
   L.space = space;
   L.conv = conv;
   L.active_jobs = active_jobs(njobs, active);
-  PROF(c, space == 2 ? PINT_PROF_MG_Q2 : PINT_PROF_MG_Q1, 1);
-  launch_mg<T>(L, c->st);
+  cudaStream_t st = stream ? stream : c->st;
+  PROF_ON(c, space == 2 ? PINT_PROF_MG_Q2 : PINT_PROF_MG_Q1, 1, st);
+  launch_mg<T>(L, st);
 }
 
 template <class T>
 void Engine<T>::cheb(int space, const FieldJob* jobs, int njobs, cpx<T>* xb, const cpx<T>* bb, const int* active,
-                     int fields_per_job) {
+                     int fields_per_job, cudaStream_t stream) {
   ChebLaunch<T> L{};
   L.tabs = tabs;
   L.t64 = c->t64;
@@ -290,8 +297,8 @@ void Engine<T>::cheb(int space, const FieldJob* jobs, int njobs, cpx<T>* xb, con
   L.lmax = space == 2 ? Q2_LMAX : Q1_LMAX;
   L.space = space;
   L.active_jobs = active_jobs(njobs, active);
-  PROF(c, PINT_PROF_CHEB, 1);
-  launch_cheb<T>(L, c->st);
+  PROF_ON(c, PINT_PROF_CHEB, 1, stream ? stream : c->st);
+  launch_cheb<T>(L, stream ? stream : c->st);
 }
 
 template <class T>
@@ -319,13 +326,21 @@ void Engine<T>::block_prec(const cpx<T>* U, cpx<T>* Out, const int* active) {
   const Slots& s = c->s;
   cudaStream_t st = c->st;
   if (!c->oseen) {
+    // The velocity and pressure parts of P~_j are independent: the pressure
+    // part runs on a second stream beside the velocity multigrid (own
+    // workspace; disjoint output slots), joined before returning.
+    cudaStream_t sa = c->st_aux;
+    cudaEventRecord(c->ev_fork, st);
+    cudaStreamWaitEvent(sa, c->ev_fork, 0);
     // W_j^{-1} on the four velocity fields (v and lambda blocks)
     mg(2, false, c->j_W4, 4 * J, Out, U, active, 1);
     // S^_j^{-1} = (1 + c1) K_p^{-1} + nu c2 M_p^{-1} on the p and mu blocks
-    mg(1, false, c->j_Kp2, 2 * J, T1, U, active, 1);
-    cheb(1, c->j_Mp2, J, T2, U, active);
-    { PROF(c, PINT_PROF_COMBO, 1); launch_lincomb<T>(J, s.nblk, s.nq, Out, s.p, T1, s.p, c->d_sa, T2, s.p, c->d_sb, active, st); }
-    { PROF(c, PINT_PROF_COMBO, 1); launch_lincomb<T>(J, s.nblk, s.nq, Out, s.mu, T1, s.mu, c->d_sa, T2, s.mu, c->d_sb, active, st); }
+    mg(1, false, c->j_Kp2, 2 * J, T1, U, active, 1, sa, mgws_q1);
+    cheb(1, c->j_Mp2, J, T2, U, active, 2, sa);
+    { PROF_ON(c, PINT_PROF_COMBO, 1, sa); launch_lincomb<T>(J, s.nblk, s.nq, Out, s.p, T1, s.p, c->d_sa, T2, s.p, c->d_sb, active, sa); }
+    { PROF_ON(c, PINT_PROF_COMBO, 1, sa); launch_lincomb<T>(J, s.nblk, s.nq, Out, s.mu, T1, s.mu, c->d_sa, T2, s.mu, c->d_sb, active, sa); }
+    cudaEventRecord(c->ev_join, sa);
+    cudaStreamWaitEvent(st, c->ev_join, 0);
     return;
   }
   // ---- Oseen: Uzawa (Eq. Uzawa11) on G^(1,1), x^(0) = 0
@@ -596,6 +611,7 @@ bool setup_engine(pint_ctx* c, Engine<T>& e, size_t mg_jobs_q2, size_t mg_jobs_q
   const size_t mgws = std::max(mg_jobs_q2 * (size_t)c->lay2.per_job, mg_jobs_q1 * (size_t)c->lay1.per_job);
   const size_t chws = std::max(cheb_jobs_q2 * (size_t)c->cheb_per_q2, cheb_jobs_q1 * (size_t)c->cheb_per_q1);
   if (!c->alloc(&e.mgws, mgws * sizeof(cpx<T>)) || !c->alloc(&e.chebws, chws * sizeof(cpx<T>))) return false;
+  if (!c->oseen && !c->alloc(&e.mgws_q1, mg_jobs_q1 * (size_t)c->lay1.per_job * sizeof(cpx<T>))) return false;
   if (c->conv) {
     T* t = nullptr;
     if (!c->alloc(&t, (size_t)c->s.nq * 9 * sizeof(T))) return false;
@@ -676,6 +692,10 @@ pint_status build(pint_ctx* c) {
   s.nblk = 4LL * s.ns + 2LL * s.nq;
 
   if (!c->cu(cudaStreamSynchronize(c->st), "stream check")) return PINT_ERR_CUDA;
+  if (!c->cu(cudaStreamCreateWithFlags(&c->st_aux, cudaStreamNonBlocking), "second stream") ||
+      !c->cu(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming), "fork event") ||
+      !c->cu(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming), "join event"))
+    return PINT_ERR_CUDA;
 
   // ---- 1-D band tables per level, FP64 and FP32
   c->t64.nlev = c->t32.nlev = c->nlev;
@@ -918,6 +938,12 @@ pint_status tc_status(pint_ctx* c) {
 void free_ctx(pint_ctx* c) {
   if (!c) return;
   if (c->st) cudaStreamSynchronize(c->st);
+  if (c->st_aux) {
+    cudaStreamSynchronize(c->st_aux);
+    cudaStreamDestroy(c->st_aux);
+  }
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_join) cudaEventDestroy(c->ev_join);
   c->drain();
   for (cudaEvent_t e : c->evpool) cudaEventDestroy(e);
   for (void* v : c->allocs) cudaFree(v);
@@ -1148,6 +1174,7 @@ size_t pint_estimate_device_bytes(const pint_params* p) {
   const MGLayout l2 = make_layout(p->level, (int)N, 2), l1 = make_layout(p->level, (int)N, 1);
   const long long mgq2 = oseen ? 2 * J : 4 * J, mgq1 = 2 * J, chq2 = oseen ? 2 * J : 2, chq1 = 2 * J;
   b += std::max(mgq2 * l2.per_job, mgq1 * l1.per_job) * cs;
+  if (!oseen) b += mgq1 * l1.per_job * cs;  // pressure multigrid beside the velocity one
   b += std::max(chq2 * 2 * ns, chq1 * 2 * nq) * cs;
   if (p->wind == PINT_WIND_RECIRC)
     for (int l = 0; l < p->level; ++l) {
