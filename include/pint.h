@@ -310,10 +310,10 @@ const char* pint_server_last_error(void);
 
 /* Autotuner of the multigrid launches (on by default, process-wide): for
  * each launch shape (space, grid, number of fields, precision, operator
- * variant) three launches after the first three (untimed: module loading,
+ * variant) six launches after the first three (untimed: module loading,
  * first touch of the workspaces) run with 256, 512 and 1024 threads per
- * CTA, timed by CUDA events on the launch stream; later launches use the
- * fastest.  Results do not depend on the choice.  pint_autotune(0) restores
+ * CTA, twice each, timed by CUDA events on the launch stream; later
+ * launches use the fastest on average.  Results do not depend on the choice.  pint_autotune(0) restores
  * the fixed heuristic (1024 threads up to one field per SM, 512 up to two,
  * else 256). */
 void pint_autotune(int on);

@@ -737,22 +737,27 @@ int cta_threads(int njobs) {
 
 // ---------------------------------------------------------------------------
 // Autotuner of the multigrid CTA size.  For each launch shape (space, finest
-// nodes per side, job count, precision, operator variant) three launches
-// after a short warm-up try 256, 512 and 1024 threads per CTA, timed by CUDA
-// events on the launch stream, and every later launch of that shape uses the
-// fastest.  The choice
+// nodes per side, job count, precision, operator variant) six launches
+// after a short warm-up try 256, 512 and 1024 threads per CTA twice each
+// (interleaved), timed by CUDA events on the launch stream, and every later
+// launch of that shape uses the fastest on average.  The choice
 // does not change the results: every node's update is the same arithmetic
 // whichever thread performs it, and the nodes of a colour are independent.
 // ---------------------------------------------------------------------------
 namespace {
 constexpr int TUNE_CAND[3] = {256, 512, 1024};
 constexpr int TUNE_WARMUP = 3;  // launches of a shape before timing (module loading, first touch)
+constexpr int TUNE_REPS = 2;    // timed launches per candidate (interleaved)
+constexpr int TUNE_SLOTS = 3 * TUNE_REPS;
 struct MgTune {
   int seen = 0;
-  int best = -1;      // index into TUNE_CAND once decided
-  int next = 0;   // next candidate to time
-  float ms[3] = {-1.f, -1.f, -1.f};
-  cudaEvent_t a[3] = {}, b[3] = {};
+  int best = -1;  // index into TUNE_CAND once decided
+  int next = 0;   // next timing slot; slot i times candidate i % 3
+  float ms[TUNE_SLOTS];
+  cudaEvent_t a[TUNE_SLOTS] = {}, b[TUNE_SLOTS] = {};
+  MgTune() {
+    for (float& v : ms) v = -1.f;
+  }
 };
 using MgKey = std::tuple<int, int, int, int, int>;  // space, n0, njobs, sizeof(T), variant
 std::mutex g_tune_mu;
@@ -771,7 +776,7 @@ int tune_pick(const MgKey& key, int fallback, int& slot, cudaEvent_t& ea, cudaEv
   }
   if (t.best < 0) {
     bool all = true;
-    for (int i = 0; i < 3; ++i) {
+    for (int i = 0; i < TUNE_SLOTS; ++i) {
       if (t.ms[i] < 0.f && i < t.next) {
         const cudaError_t q = cudaEventQuery(t.b[i]);
         if (q == cudaSuccess)
@@ -782,20 +787,23 @@ int tune_pick(const MgKey& key, int fallback, int& slot, cudaEvent_t& ea, cudaEv
       all = all && t.ms[i] >= 0.f;
     }
     if (all) {
+      float sum[3] = {0.f, 0.f, 0.f};
+      for (int i = 0; i < TUNE_SLOTS; ++i) sum[i % 3] += t.ms[i];
       t.best = 0;
       for (int i = 1; i < 3; ++i)
-        if (t.ms[i] < t.ms[t.best]) t.best = i;
-      for (int i = 0; i < 3; ++i) {
+        if (sum[i] < sum[t.best]) t.best = i;
+      for (int i = 0; i < 3; ++i) t.ms[i] = sum[i] / TUNE_REPS;  // reported: mean per candidate
+      for (int i = 0; i < TUNE_SLOTS; ++i) {
         cudaEventDestroy(t.a[i]);
         cudaEventDestroy(t.b[i]);
       }
-    } else if (t.next < 3) {
+    } else if (t.next < TUNE_SLOTS) {
       slot = t.next++;
       cudaEventCreate(&t.a[slot]);
       cudaEventCreate(&t.b[slot]);
       ea = t.a[slot];
       eb = t.b[slot];
-      return TUNE_CAND[slot];
+      return TUNE_CAND[slot % 3];
     } else {
       return fallback;  // a timing is still in flight
     }
