@@ -412,8 +412,11 @@ def serve_requests(seed, count, max_level):
         nu = float(rng.choice([1 / 50, 1 / 100])) if oseen else 1e-2
         dseed = int(rng.integers(0, 2 ** 31))
         if oseen:
-            level = max(level, 5)    # 16x16 Oseen: the inner solver stagnates (reading R24)
-            beta = min(beta, 1e-4)   # larger beta: the Q_j multigrid diverges (reading R25)
+            # 16x16 Oseen: the Uzawa/commutator inner solver stagnates (inner GMRES at its cap)
+            level = max(level, 5)
+            # beta > 1e-4: the SOR multigrid for the convection-dominated Q_j of the lowest
+            # frequencies (mass shift tau/sqrt(beta) only) does not converge and Uzawa diverges
+            beta = min(beta, 1e-4)
         out.append(dict(oseen=oseen, level=min(level, max_level), K=K, beta=beta, nu=nu, seed=dseed))
     return out
 

@@ -101,7 +101,7 @@ def fp32_arnoldi_solves(P, s, freqs, blocks, fixed_its):
     The FP32 sensitivity of the inner GMRES itself differs strongly between
     frequencies (at 64 x 64, n_t = 256 it is ~30x larger at j = K/4 than at
     j = 0): comparisons of FP32 block solves at full size are held to a bar
-    derived from this emulation (reading R23)."""
+    derived from this emulation."""
     from oracle import inexact
     saved = inexact.gmres
     inexact.gmres = _gmres_fp32_vectors

@@ -14,7 +14,7 @@ import pytest
 from gpu_pairs import (FP32_TOL, FP64_TOL, KP_FP64_TOL, fp32_arnoldi_solves, freq_blocks, make_pair, part_errors,
                        relerr, settings_of, to_dev)
 
-# FP32 bar at full size (reading R23): 10x the change of the oracle's own
+# FP32 bar at full size: 10x the change of the oracle's own
 # result when only its inner Krylov vectors are rounded to FP32, at least the
 # FP32 apply bar 1e-5.
 FP32_EMULATION_FACTOR = 10.0
@@ -219,7 +219,7 @@ def test_preconditioner_apply_full_size(prec):
         emu = relerr(to_time(fp32_arnoldi_solves(P, settings_of(G), freqs, blocks, 3)), zo)
         assert err <= max(FP32_TOL, FP32_EMULATION_FACTOR * emu), (err, emu)
     else:
-        # the pressure values pass through the K_p multigrid (reading R21)
+        # the pressure values pass through the K_p multigrid (evaluation-order bar, see gpu_pairs)
         s = layout.slots(P)
         pmask = np.zeros(got.shape[1], bool)
         for nm in ("p", "mu"):

@@ -26,7 +26,7 @@ def _request(kind, level, K, beta, nu=1e-2, prec=1, seed=0):
 
 
 # Oseen requests stay on grids where the Uzawa/commutator inner solver works
-# (on 16x16 with beta = 1e-2 its inner GMRES stagnates at j = 0, reading R24)
+# (on 16x16 with beta = 1e-2 its inner GMRES stagnates at j = 0)
 MIX = [("stokes", 4, 16, 1e-2, 1e-2, 1, 1), ("oseen", 4, 8, 1e-4, 1e-2, 1, 2), ("stokes", 3, 8, 1e-6, 1e-2, 0, 3),
        ("oseen", 3, 16, 1e-3, 2e-2, 1, 4), ("stokes", 5, 4, 1e-4, 1e-2, 1, 5), ("oseen", 5, 4, 1e-2, 2e-2, 0, 6)]
 

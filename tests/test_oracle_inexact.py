@@ -273,8 +273,8 @@ def test_pressure_multigrid_rounding_spread():
 
 
 def test_fp32_krylov_emulation_is_fp32_level():
-    """The FP32-Krylov emulation that sets the full-size FP32 bars (reading
-    R23) changes a frequency-block solve at FP32 level: above FP64 rounding,
+    """The FP32-Krylov emulation that sets the full-size FP32 bars changes a
+    frequency-block solve at FP32 level: above FP64 rounding,
     far below the inner tolerance."""
     from gpu_pairs import fp32_arnoldi_solves
     from oracle import layout
