@@ -125,21 +125,6 @@ __device__ __forceinline__ cpx<T> q2_op(const T* __restrict__ tab, int n2, int i
   return r;
 }
 
-template <class T, bool CONV>
-__device__ __forceinline__ cpx<T> q2_diag(const T* __restrict__ tab, int n2, int ix, int iy, cpx<T> a, T b,
-                                          T c) {
-  const T mx = tab[(size_t)(0 * n2 + ix) * 5 + 2], my = tab[(size_t)(0 * n2 + iy) * 5 + 2];
-  const T kx = tab[(size_t)(1 * n2 + ix) * 5 + 2], ky = tab[(size_t)(1 * n2 + iy) * 5 + 2];
-  cpx<T> r = (mx * my) * a;
-  r.x += b * (kx * my + mx * ky);
-  if (CONV) {
-    const T wx = tab[(size_t)(2 * n2 + ix) * 5 + 2], wy = tab[(size_t)(2 * n2 + iy) * 5 + 2];
-    const T xx = tab[(size_t)(3 * n2 + ix) * 5 + 2], xy = tab[(size_t)(3 * n2 + iy) * 5 + 2];
-    r.x += T(2) * c * (wx * xy - xx * wy);
-  }
-  return r;
-}
-
 // Q1 scalar operator at node (ix, iy) of a grid with n1 nodes per side:
 // a (M1 x M1) + b (K1 x M1 + M1 x K1) + 2c (W1 x X1 - X1 x W1), evaluated
 // separably.  The stiffness part uses that every row of the 1-D stiffness
@@ -195,21 +180,6 @@ __device__ __forceinline__ cpx<T> q1_op(const T* __restrict__ tab, int n1, int i
   cpx<T> r = a * accM;
   rfma(r, b, accK);
   if (CONV) rfma(r, T(2) * c, accN);
-  return r;
-}
-
-template <class T, bool CONV>
-__device__ __forceinline__ cpx<T> q1_diag(const T* __restrict__ tab, int n1, int ix, int iy, cpx<T> a, T b,
-                                          T c) {
-  const T mx = tab[(size_t)(0 * n1 + ix) * 3 + 1], my = tab[(size_t)(0 * n1 + iy) * 3 + 1];
-  const T kx = tab[(size_t)(1 * n1 + ix) * 3 + 1], ky = tab[(size_t)(1 * n1 + iy) * 3 + 1];
-  cpx<T> r = (mx * my) * a;
-  r.x += b * (kx * my + mx * ky);
-  if (CONV) {
-    const T wx = tab[(size_t)(2 * n1 + ix) * 3 + 1], wy = tab[(size_t)(2 * n1 + iy) * 3 + 1];
-    const T xx = tab[(size_t)(3 * n1 + ix) * 3 + 1], xy = tab[(size_t)(3 * n1 + iy) * 3 + 1];
-    r.x += T(2) * c * (wx * xy - xx * wy);
-  }
   return r;
 }
 
