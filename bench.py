@@ -216,6 +216,19 @@ def whole_job_rate(steps, world_size, max_ms):
     return steps * world_size / (max_ms / 1e3)
 
 
+def workload_config(name, ws):
+    """The `config` object of a bench line (both arms report the same one)."""
+    W = WORKLOADS[name]
+    N = 2 ** W["level"]
+    m = W.get("restart", 30)
+    basis = (2 * m + 1) * W["K"] * (4 * (2 * N + 1) ** 2 + 2 * (N + 1) ** 2) * 8
+    l2 = (f"inputs larger than L2 (FP64 FGMRES basis {basis / 1e9:.1f} GB)" if basis > 129e6 else
+          "inputs smaller than L2 (small parity case)")
+    return {"workload": name, "kind": "oseen" if W["kind"] else "stokes", "grid": f"{N}x{N} Q2-Q1",
+            "n_t": W["K"], "T": W["T"], "betas": W["betas"], "nu": W["nu"],
+            "outer": f"FGMRES({m}), tol 1e-8", "inner_tol": 1e-2, "l2": l2, "parallelism": f"replicas x{ws}"}
+
+
 def algorithmic_bytes_mg_q2(sizes, nlaunch_jobs, cycles, bw):
     """Per-unit figure for one V-cycle on one complex Q2 field with 2+2
     sweeps: 24 n c b_w bytes (n nodes, c = 2, b_w bytes per word)."""
@@ -362,9 +375,7 @@ def run_ours(a):
         "warmup": a.warmup, "ms_per_step": round(total_ms / a.steps, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32 preconditioner / f64 FGMRES",
         "data": "synthetic (seeded curl of 4 random sine modes)",
-        "config": {"workload": a.workload, "kind": "oseen" if W["kind"] else "stokes", "grid": f"{N}x{N} Q2-Q1", "n_t": K, "T": T,
-                   "betas": W["betas"], "nu": W["nu"], "outer": f"FGMRES({W.get('restart', 30)}), tol 1e-8", "inner_tol": 1e-2,
-                   "l2": "inputs larger than L2 (FP64 FGMRES basis 9.4 GB)", "parallelism": f"replicas x{ws}"},
+        "config": workload_config(a.workload, ws),
         "latency_ms": {"p50": round(float(np.percentile(lat, 50)), 3), "p99": round(float(np.percentile(lat, 99)), 3)},
         "outer_iterations": [inf.outer_iterations for inf in infos],
         "relres": [inf.relres for inf in infos],
@@ -541,7 +552,7 @@ def run_reference(a):
         "impl": "reference", "metric": METRIC, "value": round(v, 8), "unit": UNIT, "n_gpus": a.gpus,
         "steps": a.steps, "warmup": a.warmup, "ms_per_step": round(dt / a.steps * 1e3, 1),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": a.workload, "beta": beta},
+        "config": workload_config(a.workload, 1),
         "cpu_baseline": {"kind": "oracle", "cores": cores, "value": round(v, 8), "unit": UNIT,
                          "sample": f"one frequency-block solve per step ({dt / a.steps:.2f} s), x {K} blocks x "
                                    f"{outer_its} outer its (extrapolated)"},
