@@ -1,0 +1,52 @@
+"""Host logic of bench.py that needs no GPU: the serving stream's request
+recipe, the workload configs, the DFT report arithmetic and the gating of
+profiled DRAM traffic on the kernel source."""
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+
+def test_serving_requests_are_seeded_and_follow_the_recipe():
+    a = bench.serve_requests(0, 64, 7)
+    assert a == bench.serve_requests(0, 64, 7)          # same seed, same stream
+    assert a != bench.serve_requests(1, 64, 7)
+    for r in a:
+        assert r["K"] in (16, 32, 64, 128, 256)
+        assert 4 <= r["level"] <= 7
+        if r["oseen"]:
+            assert r["level"] >= 5 and r["beta"] <= 1e-4 and r["nu"] in (1 / 50, 1 / 100)
+        else:
+            assert 1e-6 <= r["beta"] <= 1e-2 and r["nu"] == 1e-2
+    kinds = [r["oseen"] for r in a]
+    assert 16 < sum(kinds) < 48                           # 50/50 draw
+    assert all(r["level"] <= 5 for r in bench.serve_requests(0, 64, 5))
+
+
+def test_workload_configs():
+    c = bench.workload_config("stokes64_nt256", 2)
+    assert (c["grid"], c["n_t"], c["betas"], c["parallelism"]) == ("64x64 Q2-Q1", 256, [1e-2, 1e-4, 1e-6], "replicas x2")
+    assert c["l2"].startswith("inputs larger than L2")
+    assert bench.workload_config("oseen256_nt128", 1)["outer"] == "FGMRES(20), tol 1e-8"
+
+
+class _Sizes:
+    n_t, J, n_blk = 256, 129, 75014
+
+
+def test_dft_report_arithmetic():
+    rep = bench.dft_report(_Sizes, {"dft_fwd": {"launches": 2, "timed": 2, "ms": 0.4}}, (1000.0, "x"))
+    nbytes = 256 * 75014 * 8 + 129 * 75014 * 8
+    assert rep["bytes_per_launch"] == nbytes
+    assert abs(rep["dft_fwd"]["GBps"] - nbytes / 2e-4 / 1e9) < 1.0
+    flops = 6 * 2 * 128 * 256 * 256 * ((75014 + 127) // 128)
+    assert abs(rep["dft_fwd"]["tensor_tflops_issued"] - flops / 2e-4 / 1e12) < 0.1
+
+
+def test_profiled_traffic_needs_matching_source():
+    t = bench.profiled_traffic("mg_q2b_kernel_stokes64_nt256.md", "k_mg.cu")
+    assert t is None or t > 1e9                              # None once the kernel source changed
+    assert bench.profiled_traffic("mg_q2b_kernel_stokes64_nt256.md", "k_fields.cu") is None
