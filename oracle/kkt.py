@@ -154,6 +154,65 @@ class Problem:
                 b[1, 0, c * nvc:(c + 1) * nvc] += self.Ms @ v0[c, self.vi]
         return b.ravel()
 
+    def rhs_dirichlet(self, vd, f=None, v0=None, g=None):
+        """Right-hand side with non-zero Dirichlet velocity data (the Sec. 5 problems).
+
+        The state velocity on the full Q2 grid is v_k = (interior unknowns) +
+        (boundary values g_k); the adjoint velocity is zero on the boundary.
+        The data vd, f, v0 are nodal interpolants on the full grid, so each
+        load is the full-grid mass row M_{I,:} times the nodal vector.  Write
+        kn_k for the known part of the state at t_k: g_k on the boundary and 0
+        inside for k >= 1, the whole of v0 for k = 0.  Moving the known
+        columns of the Sec. 2.2 backward-Euler equations to the right gives
+          adjoint velocity rows  tau M_{I,:} vd_k - tau M_{I,:} kn_k
+          state velocity rows    tau M_{I,:} f_k - M_{I,:} (kn_k - kn_{k-1}) - tau L_{I,:} kn_k
+          state pressure rows    -tau B_{free,:} kn_k
+        and zero adjoint pressure rows.  With g = None and v0, vd, f zero on
+        the boundary this equals `rhs`.  Shapes as in `rhs`; g: (K, 2, ns)
+        (interior entries ignored) or None.
+        """
+        K, nb, nvc, nv = self.K, self.nb, self.nvc, self.nv
+        o, vi, pf, tau = self.ops, self.vi, self.pf, self.tau
+        ns = o.grid.ns
+        bnd = np.setdiff1d(np.arange(ns), vi)
+        MI = o.M[vi]                                     # M_{I,:}
+        LI = (self.nu * o.K + o.N)[vi]                   # L_{I,:}
+        Bf = (o.Bx[pf], o.By[pf])                        # B_{free,:} per component
+
+        def known(k):
+            kn = np.zeros((2, ns))
+            if k == 0:
+                if v0 is not None:
+                    kn[:] = v0
+            elif g is not None:
+                kn[:, bnd] = g[k - 1][:, bnd]
+            return kn
+
+        b = np.zeros((2, K, nb))
+        for k in range(1, K + 1):
+            kn, kp = known(k), known(k - 1)
+            for c in range(2):
+                s = slice(c * nvc, (c + 1) * nvc)
+                b[0, k - 1, s] = tau * (MI @ vd[k - 1, c]) - tau * (MI @ kn[c])
+                load = tau * (MI @ f[k - 1, c]) if f is not None else 0.0
+                b[1, k - 1, s] = load - MI @ (kn[c] - kp[c]) - tau * (LI @ kn[c])
+            b[1, k - 1, nv:] = -tau * (Bf[0] @ kn[0] + Bf[1] @ kn[1])
+        return b.ravel()
+
+    def full_velocity(self, x, g=None):
+        """State velocity of a KKT solution x on the full Q2 grid, (K, 2, ns):
+        the interior unknowns plus the boundary values of g (Sec. 5 data)."""
+        K, nb, nvc = self.K, self.nb, self.nvc
+        ns = self.ops.grid.ns
+        X = x.reshape(2, K, nb)[0]
+        out = np.zeros((K, 2, ns))
+        if g is not None:
+            bnd = np.setdiff1d(np.arange(ns), self.vi)
+            out[:, :, bnd] = g[:, :, bnd]
+        for c in range(2):
+            out[:, c, self.vi] = X[:, c * nvc:(c + 1) * nvc]
+        return out
+
     # ----------------------------------------------------- frequency blocks
     def d(self, j):
         """j-th eigenvalue of C: d_j = 1 - exp(-2 pi i j / K)  (Sec. 3.1)."""
