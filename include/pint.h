@@ -163,6 +163,25 @@ pint_status pint_get_sizes(pint_handle h, pint_sizes* s);
 pint_status pint_set_data(pint_handle h, const double* vd_host, const double* f_host,
                           const double* v0_host);
 
+/* Problem data with a prescribed (non-zero) boundary velocity, as in the
+ * problems of Sec. 5: the closed-form velocity on the boundary in Sec. 5.1,
+ * the moving lid in Sec. 5.2.  vd_host, f_host, v0_host as in pint_set_data,
+ * but read as nodal interpolants on the whole grid: every load is the
+ * full-grid mass row times all nodal values (boundary values included).
+ * g_host: [n_t][2][n_s] velocity at t_k = k tau, only its boundary nodes
+ * read (the Dirichlet data; interior entries ignored), or NULL for zero.
+ * The boundary of v0_host is the Dirichlet data at t_0.  The known boundary
+ * columns of the Sec. 2.2 backward-Euler equations are moved to b: adjoint
+ * rows get -tau M g_k, state rows -M (g_k - g_{k-1}) - tau L g_k (k = 1 uses
+ * v_0 in place of g_0 through its load), divergence rows -tau B g_k.  The
+ * adjoint velocity is zero on the boundary.  Solutions keep zero boundary
+ * entries: the state velocity at t_k is the solution plus g_k.  Host
+ * buffers are read before the call returns.  PINT_ERR_NONFINITE on NaN/Inf
+ * input, PINT_ERR_OOM if the temporary device buffers (two KKT vectors
+ * when g is given) do not fit. */
+pint_status pint_set_data_dirichlet(pint_handle h, const double* vd_host, const double* f_host,
+                                    const double* v0_host, const double* g_host);
+
 /* Copy the assembled right-hand side b (KKT vector) to b_dev. */
 pint_status pint_get_rhs(pint_handle h, double* b_dev);
 

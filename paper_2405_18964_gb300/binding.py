@@ -77,6 +77,7 @@ _SIGS = {
     "pint_destroy": (ctypes.c_int, [_P]),
     "pint_get_sizes": (ctypes.c_int, [_P, ctypes.POINTER(Sizes)]),
     "pint_set_data": (ctypes.c_int, [_P, _P, _P, _P]),
+    "pint_set_data_dirichlet": (ctypes.c_int, [_P, _P, _P, _P, _P]),
     "pint_get_rhs": (ctypes.c_int, [_P, _P]),
     "pint_kkt_matvec": (ctypes.c_int, [_P, _P, _P]),
     "pint_apply_preconditioner": (ctypes.c_int, [_P, _P, _P]),
@@ -212,6 +213,16 @@ class Problem:
         v0 = _hptr(v0, 2 * ns)
         ptr = lambda a: a.ctypes.data_as(ctypes.c_void_p) if a is not None else None
         _check(lib().pint_set_data(self.h, ptr(vd), ptr(f), ptr(v0)), self.h)
+
+    def set_data_dirichlet(self, vd, f=None, v0=None, g=None):
+        """Data with a prescribed boundary velocity g (Sec. 5 problems); full-grid loads."""
+        K, ns = self.sizes.n_t, self.sizes.n_s
+        vd = _hptr(vd, K * 2 * ns)
+        f = _hptr(f, K * 2 * ns)
+        v0 = _hptr(v0, 2 * ns)
+        g = _hptr(g, K * 2 * ns)
+        ptr = lambda a: a.ctypes.data_as(ctypes.c_void_p) if a is not None else None
+        _check(lib().pint_set_data_dirichlet(self.h, ptr(vd), ptr(f), ptr(v0), ptr(g)), self.h)
 
     def get_rhs(self, b):
         _check(lib().pint_get_rhs(self.h, _dptr(b, "float64", self.kkt_len)), self.h)

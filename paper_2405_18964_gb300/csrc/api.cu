@@ -1235,7 +1235,16 @@ pint_status pint_get_sizes(pint_handle h, pint_sizes* s) {
   return PINT_OK;
 }
 
-pint_status pint_set_data(pint_handle h, const double* vd, const double* f, const double* v0) {
+namespace {
+
+// Uploads the problem data and builds b on the device.  full = 0: loads from
+// interior nodal values only (pint_set_data).  full = 1: loads from every
+// nodal value, and the known boundary velocity g (may be null) is lifted to
+// the right-hand side as b -= A x_g, where x_g holds g_k in the boundary
+// entries of the state-velocity slots; A x_g is the Eq. FinalA matvec on the
+// whole grid, read at the interior rows (pint_set_data_dirichlet).
+pint_status set_data_impl(pint_handle h, const double* vd, const double* f, const double* v0, const double* g,
+                          int full) {
   if (!h) {
     g_err = "null handle";
     return PINT_ERR_ARG;
@@ -1243,15 +1252,19 @@ pint_status pint_set_data(pint_handle h, const double* vd, const double* f, cons
   if (!vd) return h->fail(PINT_ERR_ARG, "vd must not be null");
   const size_t nvd = (size_t)h->K * 2 * h->s.ns, nv0 = 2 * (size_t)h->s.ns;
   for (size_t i = 0; i < nvd; ++i)
-    if (!std::isfinite(vd[i]) || (f && !std::isfinite(f[i])))
-      return h->fail(PINT_ERR_NONFINITE, "non-finite value in vd or f");
+    if (!std::isfinite(vd[i]) || (f && !std::isfinite(f[i])) || (g && !std::isfinite(g[i])))
+      return h->fail(PINT_ERR_NONFINITE, "non-finite value in vd, f or g");
   if (v0)
     for (size_t i = 0; i < nv0; ++i)
       if (!std::isfinite(v0[i])) return h->fail(PINT_ERR_NONFINITE, "non-finite value in v0");
-  double *dvd = nullptr, *df = nullptr, *dv0 = nullptr;
+  const size_t nkkt = (size_t)h->K * h->s.nblk;
+  double *dvd = nullptr, *df = nullptr, *dv0 = nullptr, *dg = nullptr, *dxg = nullptr, *dyg = nullptr;
   bool ok = cudaMalloc(&dvd, sizeof(double) * nvd) == cudaSuccess;
   if (ok && f) ok = cudaMalloc(&df, sizeof(double) * nvd) == cudaSuccess;
   if (ok && v0) ok = cudaMalloc(&dv0, sizeof(double) * nv0) == cudaSuccess;
+  if (ok && g) ok = cudaMalloc(&dg, sizeof(double) * nvd) == cudaSuccess;
+  if (ok && g) ok = cudaMalloc(&dxg, sizeof(double) * nkkt) == cudaSuccess;
+  if (ok && g) ok = cudaMalloc(&dyg, sizeof(double) * nkkt) == cudaSuccess;
   pint_status rc = PINT_OK;
   if (!ok) {
     cudaGetLastError();
@@ -1260,6 +1273,7 @@ pint_status pint_set_data(pint_handle h, const double* vd, const double* f, cons
     ok = h->cu(cudaMemcpy(dvd, vd, sizeof(double) * nvd, cudaMemcpyHostToDevice), "upload vd");
     if (ok && f) ok = h->cu(cudaMemcpy(df, f, sizeof(double) * nvd, cudaMemcpyHostToDevice), "upload f");
     if (ok && v0) ok = h->cu(cudaMemcpy(dv0, v0, sizeof(double) * nv0, cudaMemcpyHostToDevice), "upload v0");
+    if (ok && g) ok = h->cu(cudaMemcpy(dg, g, sizeof(double) * nvd, cudaMemcpyHostToDevice), "upload g");
     if (ok) {
       RhsArgs a{};
       a.tabs = h->t64;
@@ -1270,16 +1284,41 @@ pint_status pint_set_data(pint_handle h, const double* vd, const double* f, cons
       a.f = df;
       a.v0 = dv0;
       a.b = h->ob;
+      a.full = full;
       launch_rhs(a, h->st);
-      ok = h->launched("rhs") && h->cu(cudaStreamSynchronize(h->st), "rhs");
+      ok = h->launched("rhs");
     }
+    if (ok && g) {
+      ok = h->cu(cudaMemsetAsync(dxg, 0, sizeof(double) * nkkt, h->st), "clear lift");
+      if (ok) {
+        launch_lift_scatter(h->s, h->K, dg, dxg, h->st);
+        kkt(h, dxg, dyg);
+        launch_axpby(-1.0, dyg, 1.0, h->ob, (long long)nkkt, h->st);
+        ok = h->launched("lift");
+      }
+    }
+    if (ok) ok = h->cu(cudaStreamSynchronize(h->st), "rhs");
     if (!ok) rc = PINT_ERR_CUDA;
   }
   cudaFree(dvd);
   if (df) cudaFree(df);
   if (dv0) cudaFree(dv0);
+  if (dg) cudaFree(dg);
+  if (dxg) cudaFree(dxg);
+  if (dyg) cudaFree(dyg);
   if (rc == PINT_OK) h->have_data = true;
   return rc;
+}
+
+}  // namespace
+
+pint_status pint_set_data(pint_handle h, const double* vd, const double* f, const double* v0) {
+  return set_data_impl(h, vd, f, v0, nullptr, 0);
+}
+
+pint_status pint_set_data_dirichlet(pint_handle h, const double* vd, const double* f, const double* v0,
+                                    const double* g) {
+  return set_data_impl(h, vd, f, v0, g, 1);
 }
 
 pint_status pint_get_rhs(pint_handle h, double* b_dev) {

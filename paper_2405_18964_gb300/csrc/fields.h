@@ -121,8 +121,12 @@ struct RhsArgs {
   const double* f;
   const double* v0;
   double* b;
+  int full;  // 1: loads use every nodal value (M_{I,:}); 0: boundary values dropped
 };
 void launch_rhs(const RhsArgs& a, cudaStream_t st);
+// x (K blocks, zeroed by the caller) gets the boundary nodal values of
+// g [K][2][ns] in its state-velocity slots; interior entries stay 0.
+void launch_lift_scatter(const Slots& s, int K, const double* g, double* x, cudaStream_t st);
 
 // ---- misc ----------------------------------------------------------------
 // Zero the non-unknown entries (Dirichlet velocity nodes, pinned pressure)

@@ -534,6 +534,37 @@ __device__ __forceinline__ double mass_interior(const double* tab, int n2, int i
   return acc;
 }
 
+// M applied to a Q2 field at an interior node, every nodal value included
+// (the full mass row M_{I,:}).  Out-of-range stencil offsets only occur for
+// midside nodes, whose +-2 band entries are zero.
+__device__ __forceinline__ double mass_all(const double* tab, int n2, int ix, int iy, const double* x) {
+  const double* Mx = tab + (size_t)ix * 5;
+  const double* My = tab + (size_t)iy * 5;
+  double acc = 0.0;
+  for (int dy = 0; dy < 5; ++dy) {
+    const size_t r = (size_t)clampi(iy + dy - 2, 0, n2 - 1) * n2;
+    double s = 0.0;
+    for (int dx = 0; dx < 5; ++dx) s = fma(Mx[dx], x[r + clampi(ix + dx - 2, 0, n2 - 1)], s);
+    acc = fma(My[dy], s, acc);
+  }
+  return acc;
+}
+
+__device__ __forceinline__ double mass_load(bool full, const double* tab, int n2, int ix, int iy, const double* x) {
+  return full ? mass_all(tab, n2, ix, iy, x) : mass_interior(tab, n2, ix, iy, x);
+}
+
+__global__ void lift_scatter_kernel(Slots s, int K, const double* __restrict__ g, double* __restrict__ x) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int k = blockIdx.y;
+  if (i >= s.ns || k >= K) return;
+  const int ix = (int)(i % s.n2), iy = (int)(i / s.n2);
+  if (q2_interior(ix, iy, s.n2)) return;
+  double* X = x + (size_t)k * s.nblk;
+  X[s.vx + i] = g[((size_t)k * 2 + 0) * s.ns + i];
+  X[s.vy + i] = g[((size_t)k * 2 + 1) * s.ns + i];
+}
+
 __global__ void rhs_kernel(RhsArgs A) {
   const int ns = A.s.ns, n2 = A.s.n2, nq = A.s.nq;
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -550,9 +581,10 @@ __global__ void rhs_kernel(RhsArgs A) {
   for (int c = 0; c < 2; ++c) {
     double bv = 0.0, bl = 0.0;
     if (inner) {
-      bv = A.tau * mass_interior(tab, n2, ix, iy, A.vd + ((size_t)k * 2 + c) * ns);
-      if (A.f) bl = A.tau * mass_interior(tab, n2, ix, iy, A.f + ((size_t)k * 2 + c) * ns);
-      if (A.v0 && k == 0) bl += mass_interior(tab, n2, ix, iy, A.v0 + (size_t)c * ns);
+      const bool fl = A.full != 0;
+      bv = A.tau * mass_load(fl, tab, n2, ix, iy, A.vd + ((size_t)k * 2 + c) * ns);
+      if (A.f) bl = A.tau * mass_load(fl, tab, n2, ix, iy, A.f + ((size_t)k * 2 + c) * ns);
+      if (A.v0 && k == 0) bl += mass_load(fl, tab, n2, ix, iy, A.v0 + (size_t)c * ns);
     }
     B[(c ? A.s.vy : A.s.vx) + t] = bv;
     B[(c ? A.s.ly : A.s.lx) + t] = bl;
@@ -566,6 +598,10 @@ inline unsigned blocks_for(long long n, int t) { return (unsigned)((n + t - 1) /
 void launch_rhs(const RhsArgs& a, cudaStream_t st) {
   const long long n = a.s.ns > a.s.nq ? a.s.ns : a.s.nq;
   rhs_kernel<<<dim3(blocks_for(n, TPB), a.K), TPB, 0, st>>>(a);
+}
+
+void launch_lift_scatter(const Slots& s, int K, const double* g, double* x, cudaStream_t st) {
+  lift_scatter_kernel<<<dim3(blocks_for(s.ns, TPB), K), TPB, 0, st>>>(s, K, g, x);
 }
 
 // ============================ launchers ====================================

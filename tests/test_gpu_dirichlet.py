@@ -1,0 +1,113 @@
+"""GPU: the problems of Sec. 5, with a prescribed boundary velocity, through
+pint_set_data_dirichlet.  The right-hand side against the oracle's
+`rhs_dirichlet`; solutions against the oracle's direct solve and, for the
+Sec. 5.1 Stokes problem at nu = 1, against the paper's closed-form velocity
+at three refinements (a property that holds at any size)."""
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spla
+
+from gpu_pairs import relerr
+from oracle import kkt, layout
+from paper_2405_18964_gb300 import binding, inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+T = 1.0
+
+
+def make(kind, level, K, beta, nu, prec=0, T=T, **kw):
+    tau = T / (K + 1)
+    oseen = kind == "oseen"
+    P = kkt.Problem(kind, level, K, tau, beta, nu, -1.0, 1.0, "recirc" if oseen else None)
+    p = binding.default_params(kind=int(oseen), level=level, n_t=K, tau=tau, beta=beta, nu=nu, x0=-1.0, x1=1.0,
+                               wind=int(oseen), prec=prec, **kw)
+    return P, binding.Problem(p, stream=torch.cuda.current_stream().cuda_stream)
+
+
+def gpu_rhs(G, K):
+    b = torch.zeros(G.kkt_len, dtype=torch.float64, device="cuda")
+    G.get_rhs(b)
+    return b.cpu().numpy().reshape(K, -1)
+
+
+CASES = [("stokes", 3, 8), ("oseen", 3, 8), ("stokes", 2, 5), ("oseen", 4, 4)]
+
+
+@pytest.mark.parametrize("kind,level,K", CASES, ids=[f"{k}-L{l}-K{K}" for k, l, K in CASES])
+def test_rhs_matches_oracle(kind, level, K):
+    """Random data with non-zero boundary values everywhere (vd, f, v0, g)."""
+    P, G = make(kind, level, K, 1e-3, 1e-2)
+    ns = P.grid.ns
+    vd = inputs.random_vector((K, 2, ns), 21)
+    f = inputs.random_vector((K, 2, ns), 22)
+    v0 = inputs.random_vector((2, ns), 23)
+    g = inputs.random_vector((K, 2, ns), 24)
+    for args in ((vd, f, v0, g), (vd, None, None, g), (vd, f, v0, None)):
+        G.set_data_dirichlet(*args)
+        bg = gpu_rhs(G, K)
+        assert relerr(layout.to_oracle_time(P, bg), P.rhs_dirichlet(*args)) <= 1e-13
+        assert np.all(bg[:, ~layout.field_mask(P)] == 0.0)
+    G.close()
+
+
+def _mms(level, K, beta, prec, tol):
+    N, tau = 2 ** level, T / (K + 1)
+    P, G = make("stokes", level, K, beta, 1.0, prec=prec, outer_tol=tol, outer_maxit=400)
+    vd, f, v0, g = inputs.stokes_mms_data(N, K, tau, T, beta)
+    G.set_data_dirichlet(vd, f, v0, g)
+    x = torch.zeros(G.kkt_len, dtype=torch.float64, device="cuda")
+    info = G.solve(x)
+    G.close()
+    xs = layout.to_oracle_time(P, x.cpu().numpy().reshape(K, -1))
+    xn, yn = inputs.q2_nodes(N, -1.0, 1.0)
+    v = np.stack([inputs.stokes_mms_velocity(xn, yn, (k + 1) * tau, T) for k in range(K)])
+    err = np.abs(P.full_velocity(xs, g) - v).max() / np.abs(v).max()
+    return P, (vd, f, v0, g), xs, info, err
+
+
+@pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "fp32"])
+def test_manufactured_solve_matches_oracle(prec):
+    """Sec. 5.1 at nu = 1, N = 8, n_t = 15: the GPU solve to
+    1e-8 equals the oracle's direct solve within 1e-7, and both are as close
+    to the closed-form velocity as the oracle's pin says (< 1e-3)."""
+    P, data, xs, info, err = _mms(3, 15, 1e-2, prec, 1e-8)
+    b = P.rhs_dirichlet(*data)
+    A = P.kkt_matrix()
+    assert np.linalg.norm(b - A @ xs) <= 1e-8 * np.linalg.norm(b) * (1 + 1e-6)
+    xd = spla.spsolve(A.tocsc(), b)
+    assert np.linalg.norm(xs - xd) / np.linalg.norm(xd) <= 1e-7
+    assert err < 1e-3, err
+
+
+def test_manufactured_solution_convergence_on_gpu():
+    """N = 8, 16, 32 with n_t = 15, 31, 63 (tau halves with h): the velocity
+    error against the closed form falls by more than 4x per refinement, as
+    the oracle's does on the coarser grids."""
+    errs = [_mms(level, K, 1e-2, 0, 1e-11)[-1] for level, K in ((3, 15), (4, 31), (5, 63))]
+    print("GPU velocity errors vs the Sec. 5.1 closed form:", errs, flush=True)
+    assert all(b < a / 4.0 for a, b in zip(errs, errs[1:])), errs
+
+
+def test_cavity_fp32_within_one_of_fp64():
+    """Sec. 5.2 lid-driven data (recirculating wind, nu = 1/100, beta = 1e-4)
+    on 32x32, n_t = 16: both precisions reach 1e-8 (true residual recomputed by
+    the oracle) within one outer iteration of each other."""
+    K = 16
+    counts = []
+    for prec in (0, 1):
+        P, G = make("oseen", 5, K, 1e-4, 1e-2, prec=prec)
+        data = inputs.cavity_data(32, K)
+        G.set_data_dirichlet(*data)
+        x = torch.zeros(G.kkt_len, dtype=torch.float64, device="cuda")
+        info = G.solve(x)
+        G.close()
+        xs = layout.to_oracle_time(P, x.cpu().numpy().reshape(K, -1))
+        b = P.rhs_dirichlet(*data)
+        assert np.linalg.norm(b - P.kkt_matrix() @ xs) <= 1e-8 * np.linalg.norm(b) * (1 + 1e-6)
+        counts.append(info.outer_iterations)
+    assert abs(counts[0] - counts[1]) <= 1, counts

@@ -3,9 +3,11 @@ iteration count of the nested preconditioners stays essentially constant as
 n_t doubles (Tables 2-5: 3-10 FGMRES iterations from n_t = 15 to 1023), the
 average inner GMRES count stays in the same range, and the linear
 preconditioner P~_C in restarted (F)GMRES(30) degrades with n_t only for
-the largest beta (Table 1).  Our data are seeded synthetic desired states on
-Q2-Q1 grids (the paper's manufactured / lid-driven data need inhomogeneous
-Dirichlet conditions), so trends are compared, not counts."""
+the largest beta (Table 1).  Data: seeded synthetic desired states, and the
+paper's own Sec. 5.1 Stokes data and Sec. 5.2 lid-driven cavity data (with
+the recirculating wind in place of the paper's two-vortex wind).  Our grids
+are Q2-Q1 squares, not the paper's P2-P1 meshes, so trends are compared,
+not counts."""
 import numpy as np
 import pytest
 
@@ -20,16 +22,24 @@ if not torch.cuda.is_available():
 NTS = [15, 31, 63, 127]
 
 
-def _solve(kind, level, K, beta, linear=0, restart=10, prec=1, T=10.0, maxit=600):
-    """(outer iterations, average inner iterations per frequency solve, converged)."""
+def _solve(kind, level, K, beta, linear=0, restart=10, prec=1, T=10.0, maxit=600, data="synthetic"):
+    """(outer iterations, average inner iterations per frequency solve, converged).
+
+    data: "synthetic" (seeded desired state, zero boundary velocity) or
+    "paper" (Sec. 5.1 data for Stokes, Sec. 5.2 cavity data for Oseen, both
+    on [-1, 1]^2 with their boundary velocity)."""
     oseen = kind == "oseen"
-    x0, x1 = (-1.0, 1.0) if oseen else (0.0, 1.0)
+    x0, x1 = (-1.0, 1.0) if oseen or data == "paper" else (0.0, 1.0)
     tau = T / (K + 1)
     p = binding.default_params(kind=int(oseen), level=level, n_t=K, tau=tau, beta=beta, nu=1e-2, x0=x0, x1=x1,
                                wind=int(oseen), prec=prec, outer_restart=restart, linear=linear,
                                outer_maxit=maxit)
     G = binding.Problem(p, stream=torch.cuda.current_stream().cuda_stream)
-    G.set_data(inputs.desired_state(2 ** level, x0, x1, K, tau, T, seed=7))
+    if data == "paper":
+        N = 2 ** level
+        G.set_data_dirichlet(*(inputs.cavity_data(N, K) if oseen else inputs.stokes_mms_data(N, K, tau, T, beta)))
+    else:
+        G.set_data(inputs.desired_state(2 ** level, x0, x1, K, tau, T, seed=7))
     x = torch.zeros(G.kkt_len, dtype=torch.float64, device="cuda")
     info = G.solve(x, check=False)
     J = K // 2 + 1
@@ -73,3 +83,21 @@ def test_linear_preconditioner_degrades_only_for_large_beta():
     for beta in (1e-3, 1e-4):
         c = [x[0] for x in res[beta]]
         assert all(x[2] for x in res[beta]) and max(c) <= 1.5 * min(c) + 3, c
+
+
+@pytest.mark.parametrize("kind", ["stokes", "oseen"])
+def test_nested_preconditioner_with_the_papers_data(kind):
+    """Tables 2-5 with the paper's own right-hand sides: Sec. 5.1 data at
+    nu = 1e-2, T = 10 (Stokes, 16x16), Sec. 5.2 lid-driven data at T = 1
+    (Oseen, 32x32, beta <= 1e-4 as above)."""
+    level, T = (4, 10.0) if kind == "stokes" else (5, 1.0)
+    betas = (1e-1, 1e-3, 1e-4) if kind == "stokes" else (1e-4, 1e-6)
+    nts = NTS[:3]
+    for beta in betas:
+        res = [_solve(kind, level, K, beta, T=T, data="paper") for K in nts]
+        outer = [r[0] for r in res]
+        inner = [round(r[1], 1) for r in res]
+        print(f"{kind} paper data beta={beta:g}: n_t {nts} -> FGMRES(10) {outer}, av. inner {inner}", flush=True)
+        assert all(r[2] for r in res), (beta, outer)
+        assert max(outer) <= 2 * min(outer) + 4, (beta, outer)
+        assert max(inner) <= 3 * min(inner) + 5, (beta, inner)
