@@ -72,13 +72,17 @@ def _mms(level, K, beta, prec, tol):
 
 @pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "fp32"])
 def test_manufactured_solve_matches_oracle(prec):
-    """Sec. 5.1 at nu = 1, N = 8, n_t = 15: the GPU solve to
-    1e-8 equals the oracle's direct solve within 1e-7, and both are as close
-    to the closed-form velocity as the oracle's pin says (< 1e-3)."""
-    P, data, xs, info, err = _mms(3, 15, 1e-2, prec, 1e-8)
+    """Sec. 5.1 at nu = 1, N = 8, n_t = 15: the GPU solve equals the
+    oracle's direct solve within 1e-7, and both are as close to the
+    closed-form velocity as the oracle's pin says (< 1e-3).  The solve runs
+    to 1e-10: at nu = 1 this system turns a relative residual of 1e-8 into a
+    solution difference of 2.4e-7, the same with either preconditioner
+    precision, so it is the stopping point and not the arithmetic."""
+    tol = 1e-10
+    P, data, xs, info, err = _mms(3, 15, 1e-2, prec, tol)
     b = P.rhs_dirichlet(*data)
     A = P.kkt_matrix()
-    assert np.linalg.norm(b - A @ xs) <= 1e-8 * np.linalg.norm(b) * (1 + 1e-6)
+    assert np.linalg.norm(b - A @ xs) <= tol * np.linalg.norm(b) * (1 + 1e-6)
     xd = spla.spsolve(A.tocsc(), b)
     assert np.linalg.norm(xs - xd) / np.linalg.norm(xd) <= 1e-7
     assert err < 1e-3, err
@@ -86,11 +90,15 @@ def test_manufactured_solve_matches_oracle(prec):
 
 def test_manufactured_solution_convergence_on_gpu():
     """N = 8, 16, 32 with n_t = 15, 31, 63 (tau halves with h): the velocity
-    error against the closed form falls by more than 4x per refinement, as
-    the oracle's does on the coarser grids."""
+    error against the closed form falls with every refinement.  It falls by
+    more than 4x from N = 8 to 16, where the spatial error dominates (the
+    oracle's own errors on N = 2, 4, 8 fall likewise); backward Euler is
+    first order in tau, so once its error dominates a refinement gains about
+    2x (measured 8.6x, then 2.6x; bar 1.8x)."""
     errs = [_mms(level, K, 1e-2, 0, 1e-11)[-1] for level, K in ((3, 15), (4, 31), (5, 63))]
     print("GPU velocity errors vs the Sec. 5.1 closed form:", errs, flush=True)
-    assert all(b < a / 4.0 for a, b in zip(errs, errs[1:])), errs
+    assert errs[1] < errs[0] / 4.0 and errs[2] < errs[1] / 1.8, errs
+    assert errs[2] < 2e-5, errs
 
 
 def test_cavity_fp32_within_one_of_fp64():
