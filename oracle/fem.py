@@ -85,6 +85,45 @@ def recirculating_wind(x, y):
     return 2.0 * y * (1.0 - x * x), -2.0 * x * (1.0 - y * y)
 
 
+TWO_VORTEX_A = 100.0 / 99.0     # 1 / semi-axis in y of both vortices
+TWO_VORTEX_B = 100.0 / 49.0     # 1 / semi-axis in x
+
+
+def two_vortex_wind(x, y):
+    """Sec. 5.2 wind: two elliptic vortices centred at (1/2, 0) and (-1/2, 0).
+
+    c1 = 1 - sqrt((B (x - 1/2))^2 + (A y)^2), c2 likewise about x = -1/2;
+    w = c1 (A^2 y, -B^2 (x - 1/2)) where c1 >= 0, w = c2 (-A^2 y, B^2 (x + 1/2))
+    where c2 >= 0, else 0.  The printed second branch is garbled; this
+    reading is the one that makes it a divergence-free vortex about its own
+    centre, turning the other way.  w is Lipschitz, zero outside the two
+    ellipses (so on the boundary of [-1,1]^2) and divergence free.
+    """
+    A, B = TWO_VORTEX_A, TWO_VORTEX_B
+    c1 = 1.0 - np.sqrt((B * (x - 0.5)) ** 2 + (A * y) ** 2)
+    c2 = 1.0 - np.sqrt((B * (x + 0.5)) ** 2 + (A * y) ** 2)
+    wx = np.where(c1 >= 0, c1 * A * A * y, np.where(c2 >= 0, -c2 * A * A * y, 0.0))
+    wy = np.where(c1 >= 0, -c1 * B * B * (x - 0.5), np.where(c2 >= 0, c2 * B * B * (x + 0.5), 0.0))
+    return wx, wy
+
+
+def wind_by_name(name):
+    """(callable or None, skew): the wind and whether its convection matrices
+    are taken in skew-symmetric form.  The recirculating wind is a
+    polynomial that the quadrature integrates exactly, so its N is already
+    skew (w . n = 0 on the boundary, div w = 0); the two-vortex wind is not,
+    and N is replaced by (N - N^T)/2, the discrete form of the
+    skew-symmetric convection (u, w . grad v) - (v, w . grad u) / 2 terms,
+    which equals N for exact integration."""
+    if name is None:
+        return None, False
+    if name == "recirc":
+        return recirculating_wind, False
+    if name == "two_vortex":
+        return two_vortex_wind, True
+    raise ValueError(f"unknown wind {name!r}")
+
+
 # --------------------------------------------------------------------------
 # Grid and assembled operators
 # --------------------------------------------------------------------------
@@ -150,10 +189,12 @@ class Operators:
     Np: sp.csr_matrix    # Q1 convection
 
 
-def assemble(N, x0=0.0, x1=1.0, wind=None, npts=4):
+def assemble(N, x0=0.0, x1=1.0, wind=None, npts=4, skew=False):
     """Element-loop assembly of all operators on the full (unrestricted) grid.
 
-    `wind` is None (Stokes, w = 0) or a callable (x, y) -> (wx, wy).
+    `wind` is None (Stokes, w = 0) or a callable (x, y) -> (wx, wy), evaluated
+    at the npts x npts Gauss points of each element; skew: return the
+    skew-symmetric parts (N - N^T)/2, (Np - Np^T)/2 of the convection matrices.
     """
     g = Grid(N, x0, x1)
     h = g.h
@@ -211,16 +252,21 @@ def assemble(N, x0=0.0, x1=1.0, wind=None, npts=4):
         return sp.coo_matrix((v, (r, c)), shape=shape).tocsr()
 
     ns, nq = g.ns, g.nq
+    Nm = scatter(glob2, glob2, Ne, (ns, ns))
+    Npm = scatter(glob1, glob1, Npe, (nq, nq))
+    if skew:
+        Nm = (0.5 * (Nm - Nm.T)).tocsr()
+        Npm = (0.5 * (Npm - Npm.T)).tocsr()
     return Operators(
         grid=g,
         M=scatter(glob2, glob2, Me, (ns, ns)),
         K=scatter(glob2, glob2, Ke, (ns, ns)),
-        N=scatter(glob2, glob2, Ne, (ns, ns)),
+        N=Nm,
         Bx=scatter(glob1, glob2, Bxe, (nq, ns)),
         By=scatter(glob1, glob2, Bye, (nq, ns)),
         Mp=scatter(glob1, glob1, Mpe, (nq, nq)),
         Kp=scatter(glob1, glob1, Kpe, (nq, nq)),
-        Np=scatter(glob1, glob1, Npe, (nq, nq)),
+        Np=Npm,
     )
 
 

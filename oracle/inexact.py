@@ -109,11 +109,11 @@ class Multigrid:
     def __init__(self, space, level, x0, x1, wind, aM, aK, aN=0.0, pre=2, post=2, omega=1.0):
         self.space = space
         self.pre, self.post, self.omega = pre, post, omega
-        wf = fem.recirculating_wind if wind == "recirc" else None
+        wf, skew = fem.wind_by_name(wind)
         self.levels = []
         for lv in range(level, 0, -1):
             N = 2 ** lv
-            ops = fem.assemble(N, x0, x1, wf)
+            ops = fem.assemble(N, x0, x1, wf, skew=skew)
             g = ops.grid
             if space == "q2":
                 M, K, Nc = ops.M, ops.K, ops.N
@@ -376,11 +376,11 @@ class _TransposedMG(Multigrid):
     def __init__(self, P, aM, aK, aNT, s):
         self.space = "q2"
         self.pre, self.post, self.omega = s.mg_pre, s.mg_post, s.sor_omega
-        wf = fem.recirculating_wind if P.wind == "recirc" else None
+        wf, skew = fem.wind_by_name(P.wind)
         self.levels = []
         for lv in range(P.level, 0, -1):
             N = 2 ** lv
-            ops = fem.assemble(N, P.x0, P.x1, wf)
+            ops = fem.assemble(N, P.x0, P.x1, wf, skew=skew)
             g = ops.grid
             free = g.velocity_interior()
             A = (aM * ops.M + aK * ops.K + aNT * ops.N.T)[free][:, free].tocsr()

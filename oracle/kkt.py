@@ -34,8 +34,9 @@ class Problem:
     """Discrete Stokes / Oseen control problem (Sec. 2).
 
     kind: "stokes" or "oseen"; level: N = 2**level elements per side;
-    K: number of time blocks; tau, beta, nu as in the paper; wind: None or
-    "recirc" (w = (2y(1-x^2), -2x(1-y^2))).
+    K: number of time blocks; tau, beta, nu as in the paper; wind: None,
+    "recirc" (w = (2y(1-x^2), -2x(1-y^2))) or "two_vortex" (the Sec. 5.2
+    wind, `fem.two_vortex_wind`).
     """
 
     def __init__(self, kind, level, K, tau, beta, nu, x0=0.0, x1=1.0, wind=None):
@@ -48,8 +49,8 @@ class Problem:
         self.nu = float(nu)
         self.x0, self.x1 = float(x0), float(x1)
         self.wind = wind
-        wf = fem.recirculating_wind if wind == "recirc" else None
-        self.ops = fem.assemble(self.N, x0, x1, wf)
+        wf, skew = fem.wind_by_name(wind)
+        self.ops = fem.assemble(self.N, x0, x1, wf, skew=skew)
         g = self.ops.grid
         self.grid = g
         self.vi = g.velocity_interior()

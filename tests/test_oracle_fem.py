@@ -128,3 +128,54 @@ def test_assembled_jacobi_mass_spectrum_within_element_bounds(N):
         A = A.toarray()
         ev = np.linalg.eigvals(np.diag(1 / np.diag(A)) @ A).real
         assert ev.min() >= lo - 1e-12 and ev.max() <= hi + 1e-12
+
+
+def test_two_vortex_wind_properties():
+    """Sec. 5.2 wind: divergence free, zero on and near the boundary (outside
+    both ellipses), tangent to the ellipses c = const, one vortex turning each
+    way about (+-1/2, 0)."""
+    rng = np.random.default_rng(1)
+    x, y = rng.uniform(-1, 1, 400), rng.uniform(-1, 1, 400)
+    A, B = fem.TWO_VORTEX_A, fem.TWO_VORTEX_B
+    c1 = 1 - np.sqrt((B * (x - 0.5)) ** 2 + (A * y) ** 2)
+    c2 = 1 - np.sqrt((B * (x + 0.5)) ** 2 + (A * y) ** 2)
+    ok = (np.minimum(np.abs(c1), np.abs(c2)) > 1e-3) & (np.minimum(np.abs(c1 - 1), np.abs(c2 - 1)) > 1e-3)
+    x, y, c1, c2 = x[ok], y[ok], c1[ok], c2[ok]
+    w = fem.two_vortex_wind
+    e = 1e-6
+    div = (w(x + e, y)[0] - w(x - e, y)[0]) / (2 * e) + (w(x, y + e)[1] - w(x, y - e)[1]) / (2 * e)
+    assert np.abs(div).max() < 1e-7
+    wx, wy = w(x, y)
+    for c, s in ((c1, 0.5), (c2, -0.5)):
+        inside = c > 0
+        gx, gy = B * B * (x - s), A * A * y          # grad of the ellipse's level function (up to a factor)
+        assert np.abs((wx * gx + wy * gy)[inside]).max() < 1e-12
+    assert np.all(wx[(c1 < 0) & (c2 < 0)] == 0) and np.all(wy[(c1 < 0) & (c2 < 0)] == 0)
+    t = np.linspace(-1, 1, 41)
+    for bx, by in ((t, -np.ones_like(t)), (t, np.ones_like(t)), (-np.ones_like(t), t), (np.ones_like(t), t)):
+        assert np.abs(np.concatenate(w(bx, by))).max() == 0.0
+    # above each centre the flow goes +x (right vortex, clockwise) and -x (left vortex)
+    assert w(np.array([0.5]), np.array([0.3]))[0][0] > 0 > w(np.array([-0.5]), np.array([0.3]))[0][0]
+
+
+def test_two_vortex_convection():
+    """The Gauss-point convection matrix of the two-vortex wind applied to
+    the linear field x approaches M w_x as h shrinks (int phi_i w . grad x =
+    int phi_i w_x); the skew-symmetric form used for this wind is exactly
+    skew and differs from the same form at 16 x 16 Gauss points by a
+    quadrature error that shrinks with h."""
+    errs, qerrs = [], []
+    for N in (8, 16, 32):
+        raw = fem.assemble(N, -1.0, 1.0, fem.two_vortex_wind)
+        sk = fem.assemble(N, -1.0, 1.0, fem.two_vortex_wind, skew=True)
+        sk16 = fem.assemble(N, -1.0, 1.0, fem.two_vortex_wind, npts=16, skew=True)
+        g = raw.grid
+        ii = g.velocity_interior()
+        X, Y = g.q2_coords()
+        wx, wy = fem.two_vortex_wind(X, Y)
+        errs.append(max(np.abs((raw.N @ X - raw.M @ wx)[ii]).max() / np.abs(raw.M @ wx).max(),
+                        np.abs((raw.N @ Y - raw.M @ wy)[ii]).max() / np.abs(raw.M @ wy).max()))
+        assert abs(sk.N + sk.N.T).max() == 0.0 and abs(sk.Np + sk.Np.T).max() == 0.0
+        qerrs.append(abs(sk.N - sk16.N).max() / abs(sk16.N).max())
+    assert errs[0] > errs[1] > errs[2] and errs[2] < 3e-2, errs          # measured 7.8e-2, 3.3e-2, 2.0e-2 (the kink limits the rate)
+    assert qerrs[0] > qerrs[2] and qerrs[2] < 1e-2, qerrs
