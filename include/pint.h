@@ -63,10 +63,16 @@ typedef enum {
 
 typedef enum { PINT_STOKES = 0, PINT_OSEEN = 1 } pint_kind;
 
-/* Wind of the Oseen operator (Sec. 2).  RECIRC is w = (2y(1-x^2), -2x(1-y^2)),
- * divergence free and tangential on the boundary of [-1,1]^2; it requires
- * x0 = -1, x1 = 1. */
-typedef enum { PINT_WIND_NONE = 0, PINT_WIND_RECIRC = 1 } pint_wind;
+/* Wind of the Oseen operator (Sec. 2); both require x0 = -1, x1 = 1.
+ *  RECIRC       w = (2y(1-x^2), -2x(1-y^2)), divergence free and tangential on
+ *               the boundary of [-1,1]^2; a polynomial, integrated exactly.
+ *  TWO_VORTEX   the wind of the Sec. 5.2 lid-driven cavity: two elliptic
+ *               vortices about (1/2, 0) and (-1/2, 0), turning opposite ways
+ *               (the printed second branch read as the divergence-free one),
+ *               zero outside them.  Not a polynomial: the convection matrices
+ *               use the wind at 4 x 4 Gauss points per element and are taken
+ *               in skew-symmetric form (N - N^T)/2, on every multigrid level. */
+typedef enum { PINT_WIND_NONE = 0, PINT_WIND_RECIRC = 1, PINT_WIND_TWO_VORTEX = 2 } pint_wind;
 
 /* Arithmetic of the preconditioner.  The outer FGMRES (Arnoldi,
  * least-squares update, true residual) and the multigrid coarse solve are

@@ -87,6 +87,9 @@ struct pint_ctx {
   int N = 0, K = 0, J = 0, nlev = 0, m_in = 0;
   Slots s{};
   bool oseen = false, conv = false, fp32 = false;
+  bool gwind = false;                     // conv by node stencils (two-vortex wind), not separable
+  double* nst64[PINT_MAXLEV] = {};        // node-order FP64 Q2 convection stencils per level (gwind)
+  double* npst64 = nullptr;               // node-order FP64 Q1 convection stencils, finest level (gwind)
   std::vector<void*> allocs;
   size_t dev_bytes = 0;
   std::string err;
@@ -563,9 +566,10 @@ bool valid_params(const pint_params* p, std::string& why) {
   if (!(p->x1 > p->x0)) return why = "x1 must exceed x0", false;
   if (p->n_t < 1 || p->n_t > 4096) return why = "n_t must be in [1, 4096]", false;
   if (!(p->tau > 0) || !(p->beta > 0) || !(p->nu > 0)) return why = "tau, beta, nu must be positive", false;
-  if (p->wind != PINT_WIND_NONE && p->wind != PINT_WIND_RECIRC) return why = "unknown wind", false;
-  if (p->wind == PINT_WIND_RECIRC && (p->x0 != -1.0 || p->x1 != 1.0))
-    return why = "the recirculating wind requires the domain [-1,1]^2", false;
+  if (p->wind != PINT_WIND_NONE && p->wind != PINT_WIND_RECIRC && p->wind != PINT_WIND_TWO_VORTEX)
+    return why = "unknown wind", false;
+  if (p->wind != PINT_WIND_NONE && (p->x0 != -1.0 || p->x1 != 1.0))
+    return why = "the winds are defined on the domain [-1,1]^2", false;
   if (p->prec != PINT_PREC_FP64 && p->prec != PINT_PREC_FP32) return why = "unknown precision", false;
   if (p->dft_mode < PINT_DFT_AUTO || p->dft_mode > PINT_DFT_TF32X3) return why = "unknown dft_mode", false;
   if ((p->dft_mode == PINT_DFT_BF16X6 || p->dft_mode == PINT_DFT_TF32X3) &&
@@ -615,7 +619,7 @@ bool setup_engine(pint_ctx* c, Engine<T>& e, size_t mg_jobs_q2, size_t mg_jobs_q
   if (c->conv) {
     T* t = nullptr;
     if (!c->alloc(&t, (size_t)c->s.nq * 9 * sizeof(T))) return false;
-    launch_build_np2d<T>(c->t64, t, c->st);
+    launch_build_np2d<T>(c->t64, t, c->gwind ? c->npst64 : nullptr, c->st);
     e.np2d = t;
   }
   if (c->conv)
@@ -623,7 +627,7 @@ bool setup_engine(pint_ctx* c, Engine<T>& e, size_t mg_jobs_q2, size_t mg_jobs_q
       const size_t n2 = 2 * (size_t)(c->N >> l) + 1, w6 = (n2 + 5) / 6;
       T* t = nullptr;
       if (!c->alloc(&t, 36 * w6 * w6 * 25 * sizeof(T))) return false;
-      launch_build_n2d<T>(c->t64, l, t, c->st);
+      launch_build_n2d<T>(c->t64, l, t, c->gwind ? c->nst64[l] : nullptr, c->st);
       e.n2d[l] = t;
     }
   std::vector<T> cs(c->K), sn(c->K);
@@ -674,7 +678,8 @@ pint_status build(pint_ctx* c) {
   c->J = p.n_t / 2 + 1;
   c->nlev = p.level;  // grids N, N/2, ..., 2
   c->oseen = p.kind == PINT_OSEEN;
-  c->conv = p.wind == PINT_WIND_RECIRC;
+  c->conv = p.wind != PINT_WIND_NONE;
+  c->gwind = p.wind == PINT_WIND_TWO_VORTEX;
   c->fp32 = p.prec == PINT_PREC_FP32;
   c->m_in = p.fixed_inner_its > 0 ? p.fixed_inner_its : p.inner_maxit;
   const int N = c->N, J = c->J;
@@ -724,6 +729,14 @@ pint_status build(pint_ctx* c) {
     c->t64.bt = d;
     c->t32.bt = f;
   }
+  // ---- convection stencils of the two-vortex wind (Sec. 5.2), every level
+  if (c->gwind)
+    for (int l = 0; l < c->nlev; ++l) {
+      std::vector<double> q2, q1;
+      build_two_vortex_stencils(N >> l, p.x0, p.x1, q2, q1);
+      if (!c->upload(&c->nst64[l], q2) || (l == 0 && !c->upload(&c->npst64, q1)))
+        return c->fail(PINT_ERR_OOM, "device allocation failed (convection stencils)");
+    }
 
   // ---- per-frequency constants (Sec. 3.1-3.2, Sec. 4)
   const double tau = p.tau, beta = p.beta, nu = p.nu, mu = p.uzawa_mu;
@@ -762,7 +775,8 @@ pint_status build(pint_ctx* c) {
       !c->alloc(&c->d_cinv, sizeof(double) * 2 * PINT_NC_MAX * PINT_NC_MAX * c->nops))
     return c->fail(PINT_ERR_OOM, "device allocation failed (operators)");
   cudaMemsetAsync(d_status, 0, sizeof(int) * c->nops, c->st);
-  launch_coarse_setup(c->t64, c->d_ops, d_space, d_conv, c->nops, c->d_cinv, d_status, c->st);
+  launch_coarse_setup(c->t64, c->d_ops, d_space, d_conv, c->nops, c->d_cinv, d_status,
+                      c->gwind ? c->nst64[c->nlev - 1] : nullptr, c->st);
   if (!c->launched("coarse setup")) return PINT_ERR_CUDA;
   {
     std::vector<int> st_h(c->nops);
@@ -962,7 +976,8 @@ void kkt(pint_ctx* c, const double* x, double* y) {
   a.tau = c->p.tau;
   a.beta = c->p.beta;
   a.nu = c->p.nu;
-  a.conv = c->conv;
+  a.conv = c->conv && !c->gwind;
+  a.nst = c->gwind ? c->nst64[0] : nullptr;
   a.x = x;
   a.y = y;
   PROF(c, PINT_PROF_KKT_MV, 2);
@@ -1176,10 +1191,11 @@ size_t pint_estimate_device_bytes(const pint_params* p) {
   b += std::max(mgq2 * l2.per_job, mgq1 * l1.per_job) * cs;
   if (!oseen) b += mgq1 * l1.per_job * cs;  // pressure multigrid beside the velocity one
   b += std::max(chq2 * 2 * ns, chq1 * 2 * nq) * cs;
-  if (p->wind == PINT_WIND_RECIRC)
+  if (p->wind != PINT_WIND_NONE)
     for (int l = 0; l < p->level; ++l) {
       const long long n2 = 2 * (N >> l) + 1, w6 = (n2 + 5) / 6;
       b += 36 * w6 * w6 * 25 * (fp32 ? 4 : 8) + nq * 9 * 8;
+      if (p->wind == PINT_WIND_TWO_VORTEX) b += n2 * n2 * 25 * 8 + (l == 0 ? nq * 9 * 8 : 0);
     }
   return (size_t)(b + b / 20 + (64LL << 20));  // 5% + 64 MiB for tables and small state
 }

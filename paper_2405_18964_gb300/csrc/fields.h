@@ -16,7 +16,8 @@ struct KKTArgs {
   Slots s;
   int K;
   double tau, beta, nu;
-  bool conv;
+  bool conv;           // separable recirculating wind
+  const double* nst;   // or node-order FP64 convection stencils [ns][25] (general wind), else null
   const double* x;
   double* y;
 };

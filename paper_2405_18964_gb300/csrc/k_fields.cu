@@ -49,6 +49,20 @@ __device__ __forceinline__ void q2_mkn_r(const double* __restrict__ tab, int n2,
   nn *= 2.0;
 }
 
+// One row of a node-order convection stencil applied to a Q2 field at an
+// interior node (all 25 neighbours exist).
+__device__ __forceinline__ double conv_row_r(const double* __restrict__ st, int n2, int ix, int iy,
+                                             const double* __restrict__ x) {
+  double acc = 0.0;
+#pragma unroll
+  for (int dy = 0; dy < 5; ++dy) {
+    const double* row = x + (size_t)clampi(iy + dy - 2, 0, n2 - 1) * n2;
+#pragma unroll
+    for (int dx = 0; dx < 5; ++dx) acc = fma(st[dy * 5 + dx], row[clampi(ix + dx - 2, 0, n2 - 1)], acc);
+  }
+  return acc;
+}
+
 __device__ __forceinline__ void bt_op_r(const double* __restrict__ bt, int n1, int n2, int ix, int iy,
                                         const double* __restrict__ p, double& ox, double& oy) {
   const double* GT = bt + (size_t)n1 * 10;
@@ -148,6 +162,10 @@ __global__ void __launch_bounds__(TPB) kkt_q2_kernel(KKTArgs A) {
     double mv, kv, nv, ml, kl, nl;
     q2_mkn_r<CONV>(tab, n2, ix, iy, v, mv, kv, nv);
     q2_mkn_r<CONV>(tab, n2, ix, iy, l, ml, kl, nl);
+    if (A.nst) {
+      nv = conv_row_r(A.nst + (size_t)t * 25, n2, ix, iy, v);
+      nl = conv_row_r(A.nst + (size_t)t * 25, n2, ix, iy, l);
+    }
     // adjoint rows: tau M v_k + M lam_k - M lam_{k+1} + tau L^T lam_k + tau B^T mu_k
     Y[sv + t] = m1 + tau * (nu * kl - nl) + tau * (c ? btm_y : btm_x);
     // state rows: M v_k - M v_{k-1} + tau L v_k + tau B^T p_k - tau/beta M lam_k

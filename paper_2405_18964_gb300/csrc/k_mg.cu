@@ -946,26 +946,36 @@ void launch_cheb(const ChebLaunch<T>& L, cudaStream_t st) {
 // Per-node convection stencil tables (FP64 -> T), one level.
 // ---------------------------------------------------------------------------
 template <class T>
-__global__ void build_n2d_kernel(Tabs<double> t64, int l, T* out) {
+__global__ void build_n2d_kernel(Tabs<double> t64, int l, T* out, const double* __restrict__ src) {
   const int n = 2 * t64.N[l] + 1;
   const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= (long long)n * n * 25) return;
   const int k = (int)(q % 25);
   const long long node = q / 25;
   const int ix = (int)(node % n), iy = (int)(node / n);
-  const int dx = k % 5, dy = k / 5;
-  const double* tab = t64.q2[l];
-  const double wx = tab[(size_t)(2 * n + ix) * 5 + dx], xx = tab[(size_t)(3 * n + ix) * 5 + dx];
-  const double wy = tab[(size_t)(2 * n + iy) * 5 + dy], xy = tab[(size_t)(3 * n + iy) * 5 + dy];
   const BLay b = make_blay(n);
-  out[(size_t)bidx(b, ix, iy) * 25 + k] = T(2.0 * (wx * xy - xx * wy));
+  double v;
+  if (src) {
+    v = src[q];
+  } else {
+    const int dx = k % 5, dy = k / 5;
+    const double* tab = t64.q2[l];
+    const double wx = tab[(size_t)(2 * n + ix) * 5 + dx], xx = tab[(size_t)(3 * n + ix) * 5 + dx];
+    const double wy = tab[(size_t)(2 * n + iy) * 5 + dy], xy = tab[(size_t)(3 * n + iy) * 5 + dy];
+    v = 2.0 * (wx * xy - xx * wy);
+  }
+  out[(size_t)bidx(b, ix, iy) * 25 + k] = T(v);
 }
 
 template <class T>
-__global__ void build_np2d_kernel(Tabs<double> t64, T* out) {
+__global__ void build_np2d_kernel(Tabs<double> t64, T* out, const double* __restrict__ src) {
   const int n = t64.N[0] + 1;
   const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= (long long)n * n * 9) return;
+  if (src) {
+    out[q] = T(src[q]);
+    return;
+  }
   const int k = (int)(q % 9);
   const long long node = q / 9;
   const int ix = (int)(node % n), iy = (int)(node / n);
@@ -977,24 +987,24 @@ __global__ void build_np2d_kernel(Tabs<double> t64, T* out) {
 }
 
 template <class T>
-void launch_build_np2d(const Tabs<double>& t64, T* out, cudaStream_t st) {
+void launch_build_np2d(const Tabs<double>& t64, T* out, const double* src, cudaStream_t st) {
   const int n = t64.N[0] + 1;
   const long long tot = (long long)n * n * 9;
-  build_np2d_kernel<T><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(t64, out);
+  build_np2d_kernel<T><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(t64, out, src);
 }
 
 template <class T>
-void launch_build_n2d(const Tabs<double>& t64, int l, T* out, cudaStream_t st) {
+void launch_build_n2d(const Tabs<double>& t64, int l, T* out, const double* src, cudaStream_t st) {
   const int n = 2 * t64.N[l] + 1;
   const long long tot = (long long)n * n * 25;
-  build_n2d_kernel<T><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(t64, l, out);
+  build_n2d_kernel<T><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(t64, l, out, src);
 }
 
 // ---------------------------------------------------------------------------
 // Coarse-grid dense inverses (one thread per operator, FP64).
 // ---------------------------------------------------------------------------
 __global__ void coarse_setup_kernel(Tabs<double> tabs, const OpCoef* ops, const int* op_space, const int* op_conv,
-                                    int nops, double* inv, int* status) {
+                                    int nops, double* inv, int* status, const double* conv_last) {
   const int op = blockIdx.x * blockDim.x + threadIdx.x;
   if (op >= nops) return;
   const int sp = op_space[op];
@@ -1021,7 +1031,19 @@ __global__ void coarse_setup_kernel(Tabs<double> tabs, const OpCoef* ops, const 
       const int nd = node_of(u);
       const int ix = nd % n, iy = nd / n;
       cpx<double> v;
-      if (sp == 2)
+      if (sp == 2 && op_conv[op] && conv_last) {
+        // general wind: the separable mass and stiffness parts plus c times
+        // the node's convection stencil
+        v = q2_op<double, false>(tabs.q2[last], n, ix, iy, e, a, oc.b, 0.0);
+        const double* st = conv_last + (size_t)nd * 25;
+        cpx<double> acc = czero<double>();
+        for (int kk = 0; kk < 25; ++kk) {
+          const int jx = ix + kk % 5 - 2, jy = iy + kk / 5 - 2;
+          if (jx < 0 || jx >= n || jy < 0 || jy >= n) continue;
+          acc = acc + st[kk] * e[jy * n + jx];
+        }
+        v = v + oc.c * acc;
+      } else if (sp == 2)
         v = op_conv[op] ? q2_op<double, true>(tabs.q2[last], n, ix, iy, e, a, oc.b, oc.c)
                         : q2_op<double, false>(tabs.q2[last], n, ix, iy, e, a, oc.b, oc.c);
       else
@@ -1079,14 +1101,14 @@ __global__ void coarse_setup_kernel(Tabs<double> tabs, const OpCoef* ops, const 
 }
 
 void launch_coarse_setup(const Tabs<double>& tabs, const OpCoef* ops, const int* op_space, const int* op_conv,
-                         int nops, double* inv, int* status, cudaStream_t st) {
-  coarse_setup_kernel<<<(nops + 63) / 64, 64, 0, st>>>(tabs, ops, op_space, op_conv, nops, inv, status);
+                         int nops, double* inv, int* status, const double* conv_last, cudaStream_t st) {
+  coarse_setup_kernel<<<(nops + 63) / 64, 64, 0, st>>>(tabs, ops, op_space, op_conv, nops, inv, status, conv_last);
 }
 
-template void launch_build_np2d<float>(const Tabs<double>&, float*, cudaStream_t);
-template void launch_build_np2d<double>(const Tabs<double>&, double*, cudaStream_t);
-template void launch_build_n2d<float>(const Tabs<double>&, int, float*, cudaStream_t);
-template void launch_build_n2d<double>(const Tabs<double>&, int, double*, cudaStream_t);
+template void launch_build_np2d<float>(const Tabs<double>&, float*, const double*, cudaStream_t);
+template void launch_build_np2d<double>(const Tabs<double>&, double*, const double*, cudaStream_t);
+template void launch_build_n2d<float>(const Tabs<double>&, int, float*, const double*, cudaStream_t);
+template void launch_build_n2d<double>(const Tabs<double>&, int, double*, const double*, cudaStream_t);
 template void launch_mg<float>(const MGLaunch<float>&, cudaStream_t);
 template void launch_mg<double>(const MGLaunch<double>&, cudaStream_t);
 template void launch_cheb<float>(const ChebLaunch<float>&, cudaStream_t);

@@ -84,20 +84,27 @@ struct ChebLaunch {
 template <class T>
 void launch_cheb(const ChebLaunch<T>& L, cudaStream_t st);
 
-// Per-node Q2 convection stencil N = 2 (W1 (x) X1 - X1 (x) W1), formed in
-// FP64 and rounded once: out[b(ix, iy) * 25 + dy * 5 + dx] at level l, with
-// b the class-blocked node index of the multigrid layout.
+// Per-node Q2 convection stencil, formed in FP64 and rounded once:
+// out[b(ix, iy) * 25 + dy * 5 + dx] at level l, with b the class-blocked node
+// index of the multigrid layout.  src == nullptr: the recirculating wind's
+// separable N = 2 (W1 (x) X1 - X1 (x) W1); else src holds the FP64 stencils
+// of this level in node order, src[(iy * n2 + ix) * 25 + dy * 5 + dx].
 template <class T>
-void launch_build_n2d(const Tabs<double>& t64, int l, T* out, cudaStream_t st);
+void launch_build_n2d(const Tabs<double>& t64, int l, T* out, const double* src, cudaStream_t st);
 
-// Per-node Q1 convection stencil N_p = 2 (W1 (x) X1 - X1 (x) W1) on the finest
-// pressure grid, FP64 -> T: out[(iy * n1 + ix) * 9 + dy * 3 + dx].
+// Per-node Q1 convection stencil on the finest pressure grid, FP64 -> T:
+// out[(iy * n1 + ix) * 9 + dy * 3 + dx]; from the separable
+// N_p = 2 (W1 (x) X1 - X1 (x) W1) when src == nullptr, else copied from src
+// (same order).
 template <class T>
-void launch_build_np2d(const Tabs<double>& t64, T* out, cudaStream_t st);
+void launch_build_np2d(const Tabs<double>& t64, T* out, const double* src, cudaStream_t st);
 
 // Coarse-grid inverses: for each op, the dense inverse of the operator on
-// the coarsest grid (FP64, Gauss-Jordan with partial pivoting).
+// the coarsest grid (FP64, Gauss-Jordan with partial pivoting).  conv_last:
+// node-order FP64 convection stencils of the coarsest Q2 grid, or nullptr for
+// the separable recirculating wind.
 void launch_coarse_setup(const Tabs<double>& tabs, const OpCoef* ops, const int* op_space,
-                         const int* op_conv, int nops, double* inv, int* status, cudaStream_t st);
+                         const int* op_conv, int nops, double* inv, int* status, const double* conv_last,
+                         cudaStream_t st);
 
 }  // namespace pint

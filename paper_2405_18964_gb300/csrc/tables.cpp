@@ -42,7 +42,99 @@ void lin_basis(double t, double v[2], double d[2]) {
   d[1] = 1.0;
 }
 
+// 4-point Gauss-Legendre rule mapped to [0, 1]: nodes (1 -+ sqrt(3/7 +- 2/7
+// sqrt(6/5))) / 2, weights (18 -+ sqrt(30)) / 72.
+void gauss4(double xi[4], double w[4]) {
+  const double a = std::sqrt(3.0 / 7.0 - 2.0 / 7.0 * std::sqrt(6.0 / 5.0));
+  const double b = std::sqrt(3.0 / 7.0 + 2.0 / 7.0 * std::sqrt(6.0 / 5.0));
+  const double wa = (18.0 + std::sqrt(30.0)) / 72.0, wb = (18.0 - std::sqrt(30.0)) / 72.0;
+  xi[0] = 0.5 * (1.0 - b);
+  xi[1] = 0.5 * (1.0 - a);
+  xi[2] = 0.5 * (1.0 + a);
+  xi[3] = 0.5 * (1.0 + b);
+  w[0] = wb;
+  w[1] = wa;
+  w[2] = wa;
+  w[3] = wb;
+}
+
+// Sec. 5.2 wind: c1 (A^2 y, -B^2 (x - 1/2)) inside the ellipse c1 >= 0 about
+// (1/2, 0), c2 (-A^2 y, B^2 (x + 1/2)) inside c2 >= 0 about (-1/2, 0), else 0,
+// with c = 1 - sqrt((B (x -+ 1/2))^2 + (A y)^2), A = 100/99, B = 100/49.
+void two_vortex(double x, double y, double& wx, double& wy) {
+  const double A = 100.0 / 99.0, B = 100.0 / 49.0;
+  const double c1 = 1.0 - std::sqrt((B * (x - 0.5)) * (B * (x - 0.5)) + (A * y) * (A * y));
+  const double c2 = 1.0 - std::sqrt((B * (x + 0.5)) * (B * (x + 0.5)) + (A * y) * (A * y));
+  if (c1 >= 0.0) {
+    wx = c1 * A * A * y;
+    wy = -c1 * B * B * (x - 0.5);
+  } else if (c2 >= 0.0) {
+    wx = -c2 * A * A * y;
+    wy = c2 * B * B * (x + 0.5);
+  } else {
+    wx = wy = 0.0;
+  }
+}
+
+// Raw convection stencils int phi_i (w . grad phi_j) of one element family
+// (p nodes per element side: 3 for Q2, 2 for Q1; band half-width p - 1),
+// then the skew part.  Node (ix, iy) of an n x n grid, n = (p - 1) N + 1.
+void convection_stencils(int N, double x0, double x1, int p, std::vector<double>& out) {
+  const int n = (p - 1) * N + 1, hw = p - 1, bw = 2 * hw + 1, nk = bw * bw;
+  const double h = (x1 - x0) / N;
+  double xi[4], wq[4];
+  gauss4(xi, wq);
+  std::vector<double> raw((size_t)n * n * nk, 0.0);
+  double v[4][3], d[4][3];
+  for (int q = 0; q < 4; ++q) {
+    double vv[3], dd[3];
+    if (p == 3)
+      quad_basis(xi[q], vv, dd);
+    else
+      lin_basis(xi[q], vv, dd);
+    for (int a = 0; a < p; ++a) {
+      v[q][a] = vv[a];
+      d[q][a] = dd[a] / h;
+    }
+  }
+  for (int ey = 0; ey < N; ++ey)
+    for (int ex = 0; ex < N; ++ex)
+      for (int qb = 0; qb < 4; ++qb)
+        for (int qa = 0; qa < 4; ++qa) {
+          double wx, wy;
+          two_vortex(x0 + (ex + xi[qa]) * h, x0 + (ey + xi[qb]) * h, wx, wy);
+          const double W = wq[qa] * wq[qb] * h * h;
+          for (int bi = 0; bi < p; ++bi)
+            for (int ai = 0; ai < p; ++ai) {
+              const double phi = v[qa][ai] * v[qb][bi];
+              const int ix = hw * ex + ai, iy = hw * ey + bi;
+              double* row = raw.data() + ((size_t)iy * n + ix) * nk;
+              for (int bj = 0; bj < p; ++bj)
+                for (int aj = 0; aj < p; ++aj) {
+                  const double g = wx * d[qa][aj] * v[qb][bj] + wy * v[qa][aj] * d[qb][bj];
+                  row[(bj - bi + hw) * bw + (aj - ai + hw)] += W * phi * g;
+                }
+            }
+        }
+  out.assign(raw.size(), 0.0);
+  for (int iy = 0; iy < n; ++iy)
+    for (int ix = 0; ix < n; ++ix)
+      for (int dy = -hw; dy <= hw; ++dy)
+        for (int dx = -hw; dx <= hw; ++dx) {
+          const int jx = ix + dx, jy = iy + dy;
+          if (jx < 0 || jx >= n || jy < 0 || jy >= n) continue;
+          const double nij = raw[((size_t)iy * n + ix) * nk + (dy + hw) * bw + (dx + hw)];
+          const double nji = raw[((size_t)jy * n + jx) * nk + (-dy + hw) * bw + (-dx + hw)];
+          out[((size_t)iy * n + ix) * nk + (dy + hw) * bw + (dx + hw)] = 0.5 * (nij - nji);
+        }
+}
+
 }  // namespace
+
+void build_two_vortex_stencils(int N, double x0, double x1, std::vector<double>& q2, std::vector<double>& q1) {
+  convection_stencils(N, x0, x1, 3, q2);
+  convection_stencils(N, x0, x1, 2, q1);
+}
 
 void build_level_tables(int N, double x0, double x1, std::vector<double>& q2, std::vector<double>& q1) {
   const int n2 = 2 * N + 1, n1 = N + 1;

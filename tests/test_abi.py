@@ -47,9 +47,13 @@ def test_default_params_and_argument_validation():
     bad = binding.default_params(level=0)
     assert binding.lib().pint_create(ctypes.byref(bad), None, ctypes.byref(h)) == 1
     assert b"level" in binding.lib().pint_last_error(None)
-    bad = binding.default_params(kind=1, wind=1, x0=0.0, x1=1.0)
+    for wind in (1, 2):
+        bad = binding.default_params(kind=1, wind=wind, x0=0.0, x1=1.0)
+        assert binding.lib().pint_create(ctypes.byref(bad), None, ctypes.byref(h)) == 1
+        assert b"[-1,1]" in binding.lib().pint_last_error(None)
+    bad = binding.default_params(kind=1, wind=3, x0=-1.0, x1=1.0)
     assert binding.lib().pint_create(ctypes.byref(bad), None, ctypes.byref(h)) == 1
-    assert b"[-1,1]" in binding.lib().pint_last_error(None)
+    assert b"wind" in binding.lib().pint_last_error(None)
     bad = binding.default_params(prec=0, dft_mode=2)          # tensor-core DFT needs FP32
     assert binding.lib().pint_create(ctypes.byref(bad), None, ctypes.byref(h)) == 1
     assert b"dft" in binding.lib().pint_last_error(None).lower()

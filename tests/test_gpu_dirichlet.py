@@ -20,12 +20,13 @@ if not torch.cuda.is_available():
 T = 1.0
 
 
-def make(kind, level, K, beta, nu, prec=0, T=T, **kw):
+def make(kind, level, K, beta, nu, prec=0, T=T, wind="recirc", **kw):
     tau = T / (K + 1)
     oseen = kind == "oseen"
-    P = kkt.Problem(kind, level, K, tau, beta, nu, -1.0, 1.0, "recirc" if oseen else None)
+    P = kkt.Problem(kind, level, K, tau, beta, nu, -1.0, 1.0, wind if oseen else None)
+    code = {"recirc": 1, "two_vortex": 2}[wind] if oseen else 0
     p = binding.default_params(kind=int(oseen), level=level, n_t=K, tau=tau, beta=beta, nu=nu, x0=-1.0, x1=1.0,
-                               wind=int(oseen), prec=prec, **kw)
+                               wind=code, prec=prec, **kw)
     return P, binding.Problem(p, stream=torch.cuda.current_stream().cuda_stream)
 
 
@@ -35,13 +36,15 @@ def gpu_rhs(G, K):
     return b.cpu().numpy().reshape(K, -1)
 
 
-CASES = [("stokes", 3, 8), ("oseen", 3, 8), ("stokes", 2, 5), ("oseen", 4, 4)]
+CASES = [("stokes", 3, 8, None), ("oseen", 3, 8, "recirc"), ("stokes", 2, 5, None), ("oseen", 4, 4, "recirc"),
+         ("oseen", 3, 8, "two_vortex")]
 
 
-@pytest.mark.parametrize("kind,level,K", CASES, ids=[f"{k}-L{l}-K{K}" for k, l, K in CASES])
-def test_rhs_matches_oracle(kind, level, K):
-    """Random data with non-zero boundary values everywhere (vd, f, v0, g)."""
-    P, G = make(kind, level, K, 1e-3, 1e-2)
+@pytest.mark.parametrize("kind,level,K,wind", CASES, ids=[f"{k}-L{l}-K{K}-{w}" for k, l, K, w in CASES])
+def test_rhs_matches_oracle(kind, level, K, wind):
+    """Random data with non-zero boundary values everywhere (vd, f, v0, g);
+    the lift goes through the convection of each wind."""
+    P, G = make(kind, level, K, 1e-3, 1e-2, wind=wind or "recirc")
     ns = P.grid.ns
     vd = inputs.random_vector((K, 2, ns), 21)
     f = inputs.random_vector((K, 2, ns), 22)
@@ -101,14 +104,16 @@ def test_manufactured_solution_convergence_on_gpu():
     assert errs[2] < 2e-5, errs
 
 
-def test_cavity_fp32_within_one_of_fp64():
-    """Sec. 5.2 lid-driven data (recirculating wind, nu = 1/100, beta = 1e-4)
-    on 32x32, n_t = 16: both precisions reach 1e-8 (true residual recomputed by
-    the oracle) within one outer iteration of each other."""
+@pytest.mark.parametrize("wind,beta", [("two_vortex", 1e-2), ("recirc", 1e-4)])
+def test_cavity_fp32_within_one_of_fp64(wind, beta):
+    """Sec. 5.2 lid-driven data on 32x32, n_t = 16, nu = 1/100, with the
+    paper's two-vortex wind (and with the recirculating one): both precisions
+    reach 1e-8 (true residual recomputed by the oracle) within one outer
+    iteration of each other."""
     K = 16
     counts = []
     for prec in (0, 1):
-        P, G = make("oseen", 5, K, 1e-4, 1e-2, prec=prec)
+        P, G = make("oseen", 5, K, beta, 1e-2, prec=prec, wind=wind)
         data = inputs.cavity_data(32, K)
         G.set_data_dirichlet(*data)
         x = torch.zeros(G.kkt_len, dtype=torch.float64, device="cuda")

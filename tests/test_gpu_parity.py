@@ -18,7 +18,7 @@ pytestmark = pytest.mark.gpu
 if not torch.cuda.is_available():
     pytest.skip("no CUDA device", allow_module_level=True)
 
-KINDS = [("stokes", 3, 8), ("oseen", 3, 8), ("stokes", 2, 5), ("oseen", 4, 4)]
+KINDS = [("stokes", 3, 8), ("oseen", 3, 8), ("stokes", 2, 5), ("oseen", 4, 4), ("oseen-2v", 3, 8)]
 IDS = [f"{k}-L{l}-K{K}" for k, l, K in KINDS]
 
 
@@ -97,7 +97,7 @@ def test_components(kind, level, K, prec):
     J = K // 2 + 1
     q2b, q1b = inexact.mass_bounds()
     for j in sorted({0, 1, J - 1}):
-        blk = inexact.OseenBlockPreconditioner(P, j, s) if kind == "oseen" else \
+        blk = inexact.OseenBlockPreconditioner(P, j, s) if kind.startswith("oseen") else \
             inexact.StokesBlockPreconditioner(P, j, s)
         for name in _components(kind):
             q1 = name in ("mg_Kp", "cheb_Mp")
@@ -139,7 +139,7 @@ def test_block_preconditioner(kind, level, K, prec):
         x[~layout.field_mask(P)] = 0
         y = torch.zeros(nb, dtype=torch.complex128, device="cuda")
         G.component_apply("block_prec", j, to_dev(x, "complex128"), y)
-        blk = inexact.OseenBlockPreconditioner(P, j, s) if kind == "oseen" else \
+        blk = inexact.OseenBlockPreconditioner(P, j, s) if kind.startswith("oseen") else \
             inexact.StokesBlockPreconditioner(P, j, s)
         ref = blk(layout.to_oracle_freq(P, x))
         assert relerr(layout.to_oracle_freq(P, y.cpu().numpy()), ref) <= tol(prec), j
@@ -159,7 +159,7 @@ def test_preconditioner_apply(kind, level, K, linear, prec):
     G.apply_preconditioner(to_dev(r), z)
     zo = pc(layout.to_oracle_time(P, r.reshape(K, -1)))
     bar = tol(prec)
-    if prec == 1 and kind == "oseen" and not linear:
+    if prec == 1 and kind.startswith("oseen") and not linear:
         # Documented exception to the 1e-5 FP32 bar: inner GMRES on the
         # non-normal Oseen blocks amplifies the relative error of the FP32
         # Algorithm-3 preconditioner (~1e-6 on the ill-conditioned j = 0
@@ -199,7 +199,8 @@ def test_frequency_solve_tolerance_driven(kind, level, K, prec):
 
 @pytest.mark.parametrize("prec", [0, 1])
 @pytest.mark.parametrize("kind,level,K,beta", [("stokes", 3, 8, 1e-2), ("oseen", 3, 8, 1e-4),
-                                               ("stokes", 4, 16, 1e-4)], ids=["stokes", "oseen", "stokes-L4"])
+                                               ("stokes", 4, 16, 1e-4), ("oseen-2v", 3, 8, 1e-2)],
+                         ids=["stokes", "oseen", "stokes-L4", "oseen-2v"])
 def test_solve_matches_direct_solution(kind, level, K, beta, prec):
     """FGMRES to relres 1e-8: the true residual, recomputed on the CPU with
     the oracle's assembled matrix, is <= 1e-8; the solution matches the
@@ -219,7 +220,8 @@ def test_solve_matches_direct_solution(kind, level, K, beta, prec):
     assert info.relres <= 1e-8
 
 
-@pytest.mark.parametrize("kind,level,K,beta", [("stokes", 3, 8, 1e-2), ("oseen", 3, 8, 1e-4)])
+@pytest.mark.parametrize("kind,level,K,beta", [("stokes", 3, 8, 1e-2), ("oseen", 3, 8, 1e-4),
+                                               ("oseen-2v", 3, 8, 1e-2)])
 def test_fp32_outer_iterations_within_one_of_fp64(kind, level, K, beta):
     counts = []
     for prec in (0, 1):
