@@ -135,15 +135,25 @@ def peaks():
 def profiled_traffic(summary, source):
     """DRAM bytes per launch (dram__bytes_read + dram__bytes_write) from a
     committed ncu summary, or None once the kernel source has changed since
-    the counters were taken (the summary records the source's SHA-1)."""
+    the counters were taken.  The summary records the SHA-1 of the source
+    file, or, with a `kernel_source_end:` line, of the file's text before that
+    line (the part holding the kernel and everything it calls)."""
     import hashlib
     path = os.path.join(ROOT, "profiles", summary)
     src = os.path.join(ROOT, "paper_2405_18964_gb300", "csrc", source)
     if not (os.path.exists(path) and os.path.exists(src)):
         return None
-    fields = dict(ln.split(":", 1) for ln in open(path) if ln.startswith(("kernel_source_sha1:", "traffic_bytes")))
+    keys = ("kernel_source_sha1:", "kernel_source_end:", "traffic_bytes")
+    fields = dict(ln.rstrip("\n").split(":", 1) for ln in open(path) if ln.startswith(keys))
     sha = fields.get("kernel_source_sha1", "").split()[0:1]
-    if not sha or sha[0] != hashlib.sha1(open(src, "rb").read()).hexdigest():
+    text = open(src, "rb").read()
+    end = fields.get("kernel_source_end", "").strip()
+    if end:
+        i = text.find(end.encode())
+        if i < 0:
+            return None
+        text = text[:i]
+    if not sha or sha[0] != hashlib.sha1(text).hexdigest():
         return None
     return int(fields["traffic_bytes_per_launch"].strip())
 

@@ -50,3 +50,23 @@ def test_profiled_traffic_needs_matching_source():
     t = bench.profiled_traffic("mg_q2b_kernel_stokes64_nt256.md", "k_mg.cu")
     assert t is None or t > 1e9                              # None once the kernel source changed
     assert bench.profiled_traffic("mg_q2b_kernel_stokes64_nt256.md", "k_fields.cu") is None
+
+
+def test_profiled_traffic_region_gate(tmp_path, monkeypatch):
+    """With a kernel_source_end line only the text before it is hashed: edits
+    after it keep the traffic figure, edits before it drop it."""
+    import hashlib
+    (tmp_path / "profiles").mkdir()
+    csrc = tmp_path / "paper_2405_18964_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    head, marker = b"__global__ void k() {}\n", "// other kernels"
+    (csrc / "k.cu").write_bytes(head + marker.encode() + b"\nvoid f() {}\n")
+    (tmp_path / "profiles" / "k.md").write_text(
+        f"kernel_source_sha1: {hashlib.sha1(head).hexdigest()} (k.cu)\n"
+        f"kernel_source_end: {marker}\ntraffic_bytes_per_launch: 1234\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.profiled_traffic("k.md", "k.cu") == 1234
+    (csrc / "k.cu").write_bytes(head + marker.encode() + b"\nvoid f() { g(); }\n")
+    assert bench.profiled_traffic("k.md", "k.cu") == 1234
+    (csrc / "k.cu").write_bytes(b"__global__ void k() { x(); }\n" + marker.encode() + b"\n")
+    assert bench.profiled_traffic("k.md", "k.cu") is None
