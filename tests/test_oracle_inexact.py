@@ -11,8 +11,18 @@ def stokes(level=2, K=4, beta=1e-2, tau=0.2):
     return kkt.Problem("stokes", level, K, tau, beta, 1e-2, 0.0, 1.0, None)
 
 
-def oseen(level=2, K=4, beta=1e-3, tau=0.2, nu=1e-2):
-    return kkt.Problem("oseen", level, K, tau, beta, nu, -1.0, 1.0, "recirc")
+def oseen(level=2, K=4, beta=1e-3, tau=0.2, nu=1e-2, wind="recirc"):
+    return kkt.Problem("oseen", level, K, tau, beta, nu, -1.0, 1.0, wind)
+
+
+def problem(kind, level, K):
+    """kind: "stokes", "oseen" (recirculating wind) or "oseen-2v" (Sec. 5.2 wind)."""
+    if kind == "stokes":
+        return stokes(level, K)
+    return oseen(level, K, wind="two_vortex" if kind == "oseen-2v" else "recirc")
+
+
+KINDS = ["stokes", "oseen", "oseen-2v"]
 
 
 @pytest.mark.parametrize("space", ["q2", "q1"])
@@ -124,12 +134,13 @@ def test_gmres_tolerance_stop():
     assert np.linalg.norm(s - Z @ x_prev) / np.linalg.norm(s) > 1e-2
 
 
-def test_uzawa_with_exact_inner_solves_converges():
+@pytest.mark.parametrize("wind", ["recirc", "two_vortex"])
+def test_uzawa_with_exact_inner_solves_converges(wind):
     """Eq. Uzawa11 with M^ = M and S^^{-1} exact is a contraction with factor
     max |1 - lambda/mu| = 1/3 for lambda in [1/2, 1], mu = 3/4 (Sec. 4):
     it converges to the solution of G_j^(1,1) x = b."""
     g = paper_bounds()
-    P = oseen(2, 4)
+    P = oseen(2, 4, wind=wind)
     j = 1
     s = inexact.Settings(uzawa_steps=40, uzawa_mu=g["uzawa_mu"])
     B = inexact.OseenBlockPreconditioner(P, j, s)
@@ -151,10 +162,11 @@ def test_uzawa_with_exact_inner_solves_converges():
     assert np.linalg.norm(np.concatenate([y1, y2]) - xt) < 0.5 * np.linalg.norm(xt)
 
 
-def test_algorithm3_with_exact_pieces_is_block_triangular_solve():
+@pytest.mark.parametrize("wind", ["recirc", "two_vortex"])
+def test_algorithm3_with_exact_pieces_is_block_triangular_solve(wind):
     """With exact (1,1) and exact commutator Schur pieces, Algorithm 3 solves
     [[G11, 0], [G21, -S^]] y = r (reading R6)."""
-    P = oseen(1, 4)
+    P = oseen(1 if wind == "recirc" else 2, 4, wind=wind)
     j = 1
     s = inexact.Settings(uzawa_steps=60, mg_cycles=60, cheb_steps=80)
     B = inexact.OseenBlockPreconditioner(P, j, s)
@@ -175,9 +187,9 @@ def test_algorithm3_with_exact_pieces_is_block_triangular_solve():
     assert np.linalg.norm(y - yt) <= 1e-7 * np.linalg.norm(yt)
 
 
-@pytest.mark.parametrize("kind", ["stokes", "oseen"])
+@pytest.mark.parametrize("kind", KINDS)
 def test_algorithm2_with_tight_inner_tolerance_is_exact_pc(kind):
-    P = stokes(1, 4) if kind == "stokes" else oseen(1, 4)
+    P = problem(kind, 1 if kind != "oseen-2v" else 2, 4)
     s = inexact.Settings(inner_tol=1e-13, inner_maxit=200)
     pc = inexact.PinTPreconditioner(P, s)
     r = np.random.default_rng(5).standard_normal(P.n)
@@ -186,11 +198,11 @@ def test_algorithm2_with_tight_inner_tolerance_is_exact_pc(kind):
     assert np.linalg.norm(z - z_exact) <= 1e-9 * np.linalg.norm(z_exact)
 
 
-@pytest.mark.parametrize("kind", ["stokes", "oseen"])
+@pytest.mark.parametrize("kind", KINDS)
 def test_hermitian_half_suffices(kind):
     """The frequency-j solve of the conjugate right-hand side is the conjugate
     solution (G_{K-j} = conj(G_j)); the inexact nested solvers preserve this."""
-    P = stokes(2, 4) if kind == "stokes" else oseen(2, 4)
+    P = problem(kind, 2, 4)
     pc = inexact.PinTPreconditioner(P)
     g = np.random.default_rng(6).standard_normal(P.nb * 2) + 1j * np.random.default_rng(7).standard_normal(P.nb * 2)
     y1 = pc.solve_block(1, g)
@@ -198,10 +210,10 @@ def test_hermitian_half_suffices(kind):
     assert np.linalg.norm(y3 - np.conj(y1)) <= 1e-12 * np.linalg.norm(y1)
 
 
-@pytest.mark.parametrize("kind", ["stokes", "oseen"])
+@pytest.mark.parametrize("kind", KINDS)
 def test_full_solve_alg2_fgmres(kind):
     from paper_2405_18964_gb300 import inputs
-    P = stokes(2, 4) if kind == "stokes" else oseen(2, 4)
+    P = problem(kind, 2, 4)
     vd = inputs.desired_state(P.N, P.x0, P.x1, P.K, P.tau, P.tau * (P.K + 1), seed=0)
     b = P.rhs(vd)
     A = P.kkt_matrix()

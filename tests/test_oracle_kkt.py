@@ -13,14 +13,14 @@ def stokes(level=1, K=3, beta=1e-2, tau=0.25):
     return kkt.Problem("stokes", level, K, tau, beta, 1e-2, 0.0, 1.0, None)
 
 
-def oseen(level=1, K=3, beta=1e-3, tau=0.25, nu=1e-2):
-    return kkt.Problem("oseen", level, K, tau, beta, nu, -1.0, 1.0, "recirc")
+def oseen(level=1, K=3, beta=1e-3, tau=0.25, nu=1e-2, wind="recirc"):
+    return kkt.Problem("oseen", level, K, tau, beta, nu, -1.0, 1.0, wind)
 
 
-CASES = [stokes(1, 3), stokes(2, 4), oseen(1, 3), oseen(2, 4)]
+CASES = [stokes(1, 3), stokes(2, 4), oseen(1, 3), oseen(2, 4), oseen(2, 4, wind="two_vortex")]
 
 
-@pytest.mark.parametrize("P", CASES, ids=lambda P: f"{P.kind}-L{P.level}-K{P.K}")
+@pytest.mark.parametrize("P", CASES, ids=lambda P: f"{P.kind}-{P.wind}-L{P.level}-K{P.K}")
 def test_kkt_symmetric(P):
     A = P.kkt_matrix()
     assert abs(A - A.T).max() == 0.0
@@ -80,7 +80,7 @@ def test_kkt_solution_minimises_the_control_objective(P):
     assert Jw > J0 * (1 + 1e-6)
 
 
-@pytest.mark.parametrize("P", CASES, ids=lambda P: f"{P.kind}-L{P.level}-K{P.K}")
+@pytest.mark.parametrize("P", CASES, ids=lambda P: f"{P.kind}-{P.wind}-L{P.level}-K{P.K}")
 def test_circulant_identity_and_real_output(P):
     r = np.random.default_rng(1).standard_normal(P.n)
     z, Y = P.pc_inverse(r)
@@ -89,7 +89,7 @@ def test_circulant_identity_and_real_output(P):
     assert np.abs(Y.imag).max() <= 1e-12 * np.abs(Y).max()
 
 
-@pytest.mark.parametrize("P", CASES, ids=lambda P: f"{P.kind}-L{P.level}-K{P.K}")
+@pytest.mark.parametrize("P", CASES, ids=lambda P: f"{P.kind}-{P.wind}-L{P.level}-K{P.K}")
 def test_hermitian_pairing(P):
     r = np.random.default_rng(2).standard_normal(P.n).reshape(2, P.K, P.nb)
     Rh = np.fft.fft(r, axis=1)
@@ -99,7 +99,7 @@ def test_hermitian_pairing(P):
     assert abs(P.d(0)) == 0.0
 
 
-@pytest.mark.parametrize("P", CASES, ids=lambda P: f"{P.kind}-L{P.level}-K{P.K}")
+@pytest.mark.parametrize("P", CASES, ids=lambda P: f"{P.kind}-{P.wind}-L{P.level}-K{P.K}")
 def test_perturbation_rank(P):
     D = (P.kkt_matrix() - P.kkt_matrix(circulant=True)).toarray()
     assert np.linalg.matrix_rank(D) == 2 * P.nv
