@@ -107,16 +107,57 @@ def two_vortex_wind(x, y):
     return wx, wy
 
 
-def wind_by_name(name):
-    """(callable or None, skew): the wind and whether its convection matrices
-    are taken in skew-symmetric form.  The recirculating wind is a
-    polynomial that the quadrature integrates exactly, so its N is already
-    skew (w . n = 0 on the boundary, div w = 0); the two-vortex wind is not,
-    and N is replaced by (N - N^T)/2, the discrete form of the
-    skew-symmetric convection (u, w . grad v) - (v, w . grad u) / 2 terms,
-    which equals N for exact integration."""
+def q2_interpolant(W, N, x0, x1):
+    """(x, y) -> (wx, wy): the Q2 interpolant of nodal values W, shape
+    (2, (2N+1)^2) with node index iy*(2N+1)+ix, on the N x N grid of
+    [x0, x1]^2 (a caller-given nodal wind)."""
+    W = np.asarray(W, dtype=np.float64).reshape(2, 2 * N + 1, 2 * N + 1)
+    h = (x1 - x0) / N
+
+    def wind(x, y):
+        shape = np.shape(x)
+        x, y = np.ravel(x), np.ravel(y)
+        ex = np.clip(np.floor((x - x0) / h).astype(int), 0, N - 1)
+        ey = np.clip(np.floor((y - x0) / h).astype(int), 0, N - 1)
+        vx, _ = lagrange(Q2_REF_NODES, (x - x0) / h - ex)        # (3, n)
+        vy, _ = lagrange(Q2_REF_NODES, (y - x0) / h - ey)
+        out = []
+        for c in range(2):
+            acc = np.zeros_like(x)
+            for b in range(3):
+                for a in range(3):
+                    acc += vx[a] * vy[b] * W[c, 2 * ey + b, 2 * ex + a]
+            out.append(acc.reshape(shape))
+        return out[0], out[1]
+    return wind
+
+
+def inject_q2(W, N, Nc):
+    """Nodal values on the nested coarse grid with Nc elements per side: the
+    coarse Q2 nodes are fine nodes (every (N/Nc)-th), so this is a copy."""
+    r = N // Nc
+    W = np.asarray(W, dtype=np.float64).reshape(2, 2 * N + 1, 2 * N + 1)
+    return W[:, ::r, ::r].reshape(2, -1).copy()
+
+
+def wind_by_name(name, N=None, x0=None, x1=None):
+    """(callable or None, skew): the wind on the grid with N elements per side
+    of [x0, x1]^2 and whether its convection matrices are taken in
+    skew-symmetric form.  The recirculating wind is a polynomial that the
+    quadrature integrates exactly, so its N is already skew (w . n = 0 on the
+    boundary, div w = 0); for the two-vortex wind and for a caller-given
+    nodal wind it is not, and N is replaced by (N - N^T)/2, the discrete form
+    of the skew-symmetric convection (u, w . grad v) - (v, w . grad u) / 2
+    terms, which equals N for exact integration of a divergence-free wind.
+    name: None, "recirc", "two_vortex" or ("nodal", W) with W the nodal
+    values (2, (2Nf+1)^2) on the finest grid; coarser grids use the Q2
+    interpolant of the injected nodal values."""
     if name is None:
         return None, False
+    if isinstance(name, tuple) and name[0] == "nodal":
+        W = np.asarray(name[1], dtype=np.float64).reshape(2, -1)
+        Nf = (int(round(np.sqrt(W.shape[1]))) - 1) // 2
+        return q2_interpolant(inject_q2(W, Nf, N), N, x0, x1), True
     if name == "recirc":
         return recirculating_wind, False
     if name == "two_vortex":

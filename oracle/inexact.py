@@ -109,10 +109,10 @@ class Multigrid:
     def __init__(self, space, level, x0, x1, wind, aM, aK, aN=0.0, pre=2, post=2, omega=1.0):
         self.space = space
         self.pre, self.post, self.omega = pre, post, omega
-        wf, skew = fem.wind_by_name(wind)
         self.levels = []
         for lv in range(level, 0, -1):
             N = 2 ** lv
+            wf, skew = fem.wind_by_name(wind, N, x0, x1)
             ops = fem.assemble(N, x0, x1, wf, skew=skew)
             g = ops.grid
             if space == "q2":
@@ -376,10 +376,10 @@ class _TransposedMG(Multigrid):
     def __init__(self, P, aM, aK, aNT, s):
         self.space = "q2"
         self.pre, self.post, self.omega = s.mg_pre, s.mg_post, s.sor_omega
-        wf, skew = fem.wind_by_name(P.wind)
         self.levels = []
         for lv in range(P.level, 0, -1):
             N = 2 ** lv
+            wf, skew = fem.wind_by_name(P.wind, N, P.x0, P.x1)
             ops = fem.assemble(N, P.x0, P.x1, wf, skew=skew)
             g = ops.grid
             free = g.velocity_interior()

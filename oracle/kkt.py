@@ -35,8 +35,9 @@ class Problem:
 
     kind: "stokes" or "oseen"; level: N = 2**level elements per side;
     K: number of time blocks; tau, beta, nu as in the paper; wind: None,
-    "recirc" (w = (2y(1-x^2), -2x(1-y^2))) or "two_vortex" (the Sec. 5.2
-    wind, `fem.two_vortex_wind`).
+    "recirc" (w = (2y(1-x^2), -2x(1-y^2))), "two_vortex" (the Sec. 5.2
+    wind, `fem.two_vortex_wind`) or ("nodal", W), W the wind's values at the
+    Q2 nodes, shape (2, (2N+1)^2) (`fem.wind_by_name`).
     """
 
     def __init__(self, kind, level, K, tau, beta, nu, x0=0.0, x1=1.0, wind=None):
@@ -49,7 +50,7 @@ class Problem:
         self.nu = float(nu)
         self.x0, self.x1 = float(x0), float(x1)
         self.wind = wind
-        wf, skew = fem.wind_by_name(wind)
+        wf, skew = fem.wind_by_name(wind, self.N, x0, x1)
         self.ops = fem.assemble(self.N, x0, x1, wf, skew=skew)
         g = self.ops.grid
         self.grid = g

@@ -179,3 +179,33 @@ def test_two_vortex_convection():
         qerrs.append(abs(sk.N - sk16.N).max() / abs(sk16.N).max())
     assert errs[0] > errs[1] > errs[2] and errs[2] < 3e-2, errs          # measured 7.8e-2, 3.3e-2, 2.0e-2 (the kink limits the rate)
     assert qerrs[0] > qerrs[2] and qerrs[2] < 1e-2, qerrs
+
+
+def test_nodal_wind_reproduces_the_polynomial_wind():
+    """A caller-given nodal wind is used through its Q2 interpolant, injected
+    to coarser grids.  The recirculating wind is a quadratic, so its nodal
+    values reproduce it exactly on every level: the convection matrices equal
+    the analytic ones (the skew-symmetric form changes nothing for an exactly
+    skew N), on the fine grid and on every multigrid level."""
+    from oracle import inexact, kkt
+    N = 8
+    g = fem.Grid(N, -1.0, 1.0)
+    X, Y = g.q2_coords()
+    W = np.stack(fem.recirculating_wind(X, Y))
+    Pn = kkt.Problem("oseen", 3, 4, 0.2, 1e-3, 1e-2, -1.0, 1.0, ("nodal", W))
+    Pr = kkt.Problem("oseen", 3, 4, 0.2, 1e-3, 1e-2, -1.0, 1.0, "recirc")
+    scale = abs(Pr.ops.N).max()
+    assert abs(Pn.ops.N - Pr.ops.N).max() <= 1e-14 * scale
+    assert abs(Pn.ops.Np - Pr.ops.Np).max() <= 1e-14 * abs(Pr.ops.Np).max()
+    mn = inexact.Multigrid("q2", 3, -1.0, 1.0, ("nodal", W), 1.0 + 0.5j, 0.01, 0.2)
+    mr = inexact.Multigrid("q2", 3, -1.0, 1.0, "recirc", 1.0 + 0.5j, 0.01, 0.2)
+    assert len(mn.levels) == 3
+    for a, b in zip(mn.levels, mr.levels):
+        assert abs(a.A - b.A).max() <= 1e-14 * abs(b.A).max()
+    # a nodal field that is not a quadratic gives an exactly skew N and
+    # differs from the analytic wind's operator by the interpolation error
+    W2 = np.stack(fem.two_vortex_wind(X, Y))
+    P2 = kkt.Problem("oseen", 3, 4, 0.2, 1e-3, 1e-2, -1.0, 1.0, ("nodal", W2))
+    assert abs(P2.ops.N + P2.ops.N.T).max() == 0.0
+    Pa = kkt.Problem("oseen", 3, 4, 0.2, 1e-3, 1e-2, -1.0, 1.0, "two_vortex")
+    assert 0 < abs(P2.ops.N - Pa.ops.N).max() < 0.2 * abs(Pa.ops.N).max()
