@@ -63,7 +63,8 @@ typedef enum {
 
 typedef enum { PINT_STOKES = 0, PINT_OSEEN = 1 } pint_kind;
 
-/* Wind of the Oseen operator (Sec. 2); both require x0 = -1, x1 = 1.
+/* Wind of the Oseen operator (Sec. 2); RECIRC and TWO_VORTEX require
+ * x0 = -1, x1 = 1.
  *  RECIRC       w = (2y(1-x^2), -2x(1-y^2)), divergence free and tangential on
  *               the boundary of [-1,1]^2; a polynomial, integrated exactly.
  *  TWO_VORTEX   the wind of the Sec. 5.2 lid-driven cavity: two elliptic
@@ -71,8 +72,14 @@ typedef enum { PINT_STOKES = 0, PINT_OSEEN = 1 } pint_kind;
  *               (the printed second branch read as the divergence-free one),
  *               zero outside them.  Not a polynomial: the convection matrices
  *               use the wind at 4 x 4 Gauss points per element and are taken
- *               in skew-symmetric form (N - N^T)/2, on every multigrid level. */
-typedef enum { PINT_WIND_NONE = 0, PINT_WIND_RECIRC = 1, PINT_WIND_TWO_VORTEX = 2 } pint_wind;
+ *               in skew-symmetric form (N - N^T)/2, on every multigrid level.
+ *  NODAL        a caller-given wind: its values at the Q2 nodes of the
+ *               finest grid (pint_create_wind), used as their Q2 interpolant
+ *               and injected to the nested coarser grids; convection as for
+ *               TWO_VORTEX (same Gauss points, skew-symmetric form).  Any
+ *               domain; the wind should be (nearly) divergence free with
+ *               w . n = 0 on the boundary, as Sec. 2 assumes. */
+typedef enum { PINT_WIND_NONE = 0, PINT_WIND_RECIRC = 1, PINT_WIND_TWO_VORTEX = 2, PINT_WIND_NODAL = 3 } pint_wind;
 
 /* Arithmetic of the preconditioner.  The outer FGMRES (Arnoldi,
  * least-squares update, true residual) and the multigrid coarse solve are
@@ -154,6 +161,13 @@ void pint_default_params(pint_params* p);
  * device workspace; returns PINT_ERR_ARG for invalid parameters,
  * PINT_ERR_OOM if the workspace does not fit. */
 pint_status pint_create(const pint_params* p, void* stream, pint_handle* out);
+
+/* pint_create for p->wind = PINT_WIND_NODAL: wind_host holds the wind at the
+ * Q2 nodes of the finest grid, [2][n_s] (component, then node index
+ * iy*(2N+1)+ix), read before the call returns.  PINT_ERR_ARG if wind_host is
+ * NULL or p->wind is not PINT_WIND_NODAL (pint_create returns PINT_ERR_ARG
+ * for PINT_WIND_NODAL); PINT_ERR_NONFINITE on NaN/Inf values. */
+pint_status pint_create_wind(const pint_params* p, const double* wind_host, void* stream, pint_handle* out);
 
 /* Frees everything the handle owns.  Accepts NULL. */
 pint_status pint_destroy(pint_handle h);

@@ -76,6 +76,7 @@ _SIGS = {
     "pint_create": (ctypes.c_int, [ctypes.POINTER(Params), _P, ctypes.POINTER(_P)]),
     "pint_destroy": (ctypes.c_int, [_P]),
     "pint_get_sizes": (ctypes.c_int, [_P, ctypes.POINTER(Sizes)]),
+    "pint_create_wind": (ctypes.c_int, [ctypes.POINTER(Params), _P, _P, ctypes.POINTER(_P)]),
     "pint_set_data": (ctypes.c_int, [_P, _P, _P, _P]),
     "pint_set_data_dirichlet": (ctypes.c_int, [_P, _P, _P, _P, _P]),
     "pint_get_rhs": (ctypes.c_int, [_P, _P]),
@@ -176,11 +177,19 @@ def default_params(**kw):
 class Problem:
     """One discrete control problem on the GPU (handle of the C ABI)."""
 
-    def __init__(self, params, stream=None):
+    def __init__(self, params, stream=None, wind=None):
+        """wind: for params.wind = PINT_WIND_NODAL (3), the wind's values at
+        the finest Q2 nodes, shape (2, (2N+1)^2)."""
         self.params = params
         h = ctypes.c_void_p()
         st = ctypes.c_void_p(stream) if stream else None
-        _check(lib().pint_create(ctypes.byref(params), st, ctypes.byref(h)))
+        if wind is None:
+            _check(lib().pint_create(ctypes.byref(params), st, ctypes.byref(h)))
+        else:
+            n2 = 2 * 2 ** params.level + 1
+            w = _hptr(wind, 2 * n2 * n2)
+            _check(lib().pint_create_wind(ctypes.byref(params), w.ctypes.data_as(ctypes.c_void_p), st,
+                                          ctypes.byref(h)))
         self.h = h
         s = Sizes()
         _check(lib().pint_get_sizes(self.h, ctypes.byref(s)), self.h)

@@ -87,7 +87,8 @@ struct pint_ctx {
   int N = 0, K = 0, J = 0, nlev = 0, m_in = 0;
   Slots s{};
   bool oseen = false, conv = false, fp32 = false;
-  bool gwind = false;                     // conv by node stencils (two-vortex wind), not separable
+  bool gwind = false;                     // conv by node stencils (two-vortex or nodal wind), not separable
+  std::vector<double> wind_nodal;         // PINT_WIND_NODAL: [2][n_s] values at the finest Q2 nodes
   double* nst64[PINT_MAXLEV] = {};        // node-order FP64 Q2 convection stencils per level (gwind)
   double* npst64 = nullptr;               // node-order FP64 Q1 convection stencils, finest level (gwind)
   std::vector<void*> allocs;
@@ -566,10 +567,11 @@ bool valid_params(const pint_params* p, std::string& why) {
   if (!(p->x1 > p->x0)) return why = "x1 must exceed x0", false;
   if (p->n_t < 1 || p->n_t > 4096) return why = "n_t must be in [1, 4096]", false;
   if (!(p->tau > 0) || !(p->beta > 0) || !(p->nu > 0)) return why = "tau, beta, nu must be positive", false;
-  if (p->wind != PINT_WIND_NONE && p->wind != PINT_WIND_RECIRC && p->wind != PINT_WIND_TWO_VORTEX)
+  if (p->wind != PINT_WIND_NONE && p->wind != PINT_WIND_RECIRC && p->wind != PINT_WIND_TWO_VORTEX &&
+      p->wind != PINT_WIND_NODAL)
     return why = "unknown wind", false;
-  if (p->wind != PINT_WIND_NONE && (p->x0 != -1.0 || p->x1 != 1.0))
-    return why = "the winds are defined on the domain [-1,1]^2", false;
+  if ((p->wind == PINT_WIND_RECIRC || p->wind == PINT_WIND_TWO_VORTEX) && (p->x0 != -1.0 || p->x1 != 1.0))
+    return why = "the built-in winds are defined on the domain [-1,1]^2", false;
   if (p->prec != PINT_PREC_FP64 && p->prec != PINT_PREC_FP32) return why = "unknown precision", false;
   if (p->dft_mode < PINT_DFT_AUTO || p->dft_mode > PINT_DFT_TF32X3) return why = "unknown dft_mode", false;
   if ((p->dft_mode == PINT_DFT_BF16X6 || p->dft_mode == PINT_DFT_TF32X3) &&
@@ -679,7 +681,7 @@ pint_status build(pint_ctx* c) {
   c->nlev = p.level;  // grids N, N/2, ..., 2
   c->oseen = p.kind == PINT_OSEEN;
   c->conv = p.wind != PINT_WIND_NONE;
-  c->gwind = p.wind == PINT_WIND_TWO_VORTEX;
+  c->gwind = p.wind == PINT_WIND_TWO_VORTEX || p.wind == PINT_WIND_NODAL;
   c->fp32 = p.prec == PINT_PREC_FP32;
   c->m_in = p.fixed_inner_its > 0 ? p.fixed_inner_its : p.inner_maxit;
   const int N = c->N, J = c->J;
@@ -729,11 +731,23 @@ pint_status build(pint_ctx* c) {
     c->t64.bt = d;
     c->t32.bt = f;
   }
-  // ---- convection stencils of the two-vortex wind (Sec. 5.2), every level
+  // ---- convection stencils of the two-vortex wind (Sec. 5.2) or of a nodal
+  // wind (its values injected to each coarser grid), every level
   if (c->gwind)
     for (int l = 0; l < c->nlev; ++l) {
       std::vector<double> q2, q1;
-      build_two_vortex_stencils(N >> l, p.x0, p.x1, q2, q1);
+      if (p.wind == PINT_WIND_NODAL) {
+        const int nf = 2 * N + 1, nl = 2 * (N >> l) + 1, r = 1 << l;
+        std::vector<double> wl(2 * (size_t)nl * nl);
+        for (int comp = 0; comp < 2; ++comp)
+          for (int iy = 0; iy < nl; ++iy)
+            for (int ix = 0; ix < nl; ++ix)
+              wl[((size_t)comp * nl + iy) * nl + ix] =
+                  c->wind_nodal[((size_t)comp * nf + (size_t)iy * r) * nf + (size_t)ix * r];
+        build_nodal_wind_stencils(N >> l, p.x0, p.x1, wl.data(), q2, q1);
+      } else {
+        build_two_vortex_stencils(N >> l, p.x0, p.x1, q2, q1);
+      }
       if (!c->upload(&c->nst64[l], q2) || (l == 0 && !c->upload(&c->npst64, q1)))
         return c->fail(PINT_ERR_OOM, "device allocation failed (convection stencils)");
     }
@@ -1195,12 +1209,15 @@ size_t pint_estimate_device_bytes(const pint_params* p) {
     for (int l = 0; l < p->level; ++l) {
       const long long n2 = 2 * (N >> l) + 1, w6 = (n2 + 5) / 6;
       b += 36 * w6 * w6 * 25 * (fp32 ? 4 : 8) + nq * 9 * 8;
-      if (p->wind == PINT_WIND_TWO_VORTEX) b += n2 * n2 * 25 * 8 + (l == 0 ? nq * 9 * 8 : 0);
+      if (p->wind == PINT_WIND_TWO_VORTEX || p->wind == PINT_WIND_NODAL)
+        b += n2 * n2 * 25 * 8 + (l == 0 ? nq * 9 * 8 : 0);
     }
   return (size_t)(b + b / 20 + (64LL << 20));  // 5% + 64 MiB for tables and small state
 }
 
-pint_status pint_create(const pint_params* p, void* stream, pint_handle* out) {
+namespace {
+
+pint_status create_impl(const pint_params* p, const double* wind, void* stream, pint_handle* out) {
   if (!out) {
     g_err = "null output handle";
     return PINT_ERR_ARG;
@@ -1211,6 +1228,17 @@ pint_status pint_create(const pint_params* p, void* stream, pint_handle* out) {
     g_err = why;
     return PINT_ERR_ARG;
   }
+  if ((p->wind == PINT_WIND_NODAL) != (wind != nullptr)) {
+    g_err = wind ? "a nodal wind needs p->wind = PINT_WIND_NODAL"
+                 : "PINT_WIND_NODAL needs the wind's nodal values (pint_create_wind)";
+    return PINT_ERR_ARG;
+  }
+  const size_t nw = wind ? 2 * (size_t)((2 << p->level) + 1) * ((2 << p->level) + 1) : 0;
+  for (size_t i = 0; i < nw; ++i)
+    if (!std::isfinite(wind[i])) {
+      g_err = "non-finite value in the nodal wind";
+      return PINT_ERR_NONFINITE;
+    }
   pint_ctx* c = new (std::nothrow) pint_ctx();
   if (!c) {
     g_err = "host allocation failed";
@@ -1218,6 +1246,7 @@ pint_status pint_create(const pint_params* p, void* stream, pint_handle* out) {
   }
   c->p = *p;
   c->st = static_cast<cudaStream_t>(stream);
+  if (wind) c->wind_nodal.assign(wind, wind + nw);
   pint_status s = build(c);
   if (s != PINT_OK) {
     std::string m = c->err;
@@ -1227,6 +1256,20 @@ pint_status pint_create(const pint_params* p, void* stream, pint_handle* out) {
   }
   *out = c;
   return PINT_OK;
+}
+
+}  // namespace
+
+pint_status pint_create(const pint_params* p, void* stream, pint_handle* out) {
+  return create_impl(p, nullptr, stream, out);
+}
+
+pint_status pint_create_wind(const pint_params* p, const double* wind_host, void* stream, pint_handle* out) {
+  if (!wind_host) {
+    g_err = "wind_host must not be null";
+    return PINT_ERR_ARG;
+  }
+  return create_impl(p, wind_host, stream, out);
 }
 
 pint_status pint_destroy(pint_handle h) {

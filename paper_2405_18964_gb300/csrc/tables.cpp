@@ -76,10 +76,31 @@ void two_vortex(double x, double y, double& wx, double& wy) {
   }
 }
 
+// Wind at Gauss point (qa, qb) of element (ex, ey): the two-vortex formula
+// (wind == nullptr), or the Q2 interpolant of nodal values wind[2][(2N+1)^2].
+void wind_at(int N, double x0, double h, const double* wind, int ex, int ey, const double xi[4], int qa, int qb,
+             double& wx, double& wy) {
+  if (!wind) {
+    two_vortex(x0 + (ex + xi[qa]) * h, x0 + (ey + xi[qb]) * h, wx, wy);
+    return;
+  }
+  const int n2 = 2 * N + 1;
+  double va[3], vb[3], d[3];
+  quad_basis(xi[qa], va, d);
+  quad_basis(xi[qb], vb, d);
+  wx = wy = 0.0;
+  for (int b = 0; b < 3; ++b)
+    for (int a = 0; a < 3; ++a) {
+      const size_t node = (size_t)(2 * ey + b) * n2 + (2 * ex + a);
+      wx += va[a] * vb[b] * wind[node];
+      wy += va[a] * vb[b] * wind[(size_t)n2 * n2 + node];
+    }
+}
+
 // Raw convection stencils int phi_i (w . grad phi_j) of one element family
 // (p nodes per element side: 3 for Q2, 2 for Q1; band half-width p - 1),
 // then the skew part.  Node (ix, iy) of an n x n grid, n = (p - 1) N + 1.
-void convection_stencils(int N, double x0, double x1, int p, std::vector<double>& out) {
+void convection_stencils(int N, double x0, double x1, int p, const double* wind, std::vector<double>& out) {
   const int n = (p - 1) * N + 1, hw = p - 1, bw = 2 * hw + 1, nk = bw * bw;
   const double h = (x1 - x0) / N;
   double xi[4], wq[4];
@@ -102,7 +123,7 @@ void convection_stencils(int N, double x0, double x1, int p, std::vector<double>
       for (int qb = 0; qb < 4; ++qb)
         for (int qa = 0; qa < 4; ++qa) {
           double wx, wy;
-          two_vortex(x0 + (ex + xi[qa]) * h, x0 + (ey + xi[qb]) * h, wx, wy);
+          wind_at(N, x0, h, wind, ex, ey, xi, qa, qb, wx, wy);
           const double W = wq[qa] * wq[qb] * h * h;
           for (int bi = 0; bi < p; ++bi)
             for (int ai = 0; ai < p; ++ai) {
@@ -132,8 +153,14 @@ void convection_stencils(int N, double x0, double x1, int p, std::vector<double>
 }  // namespace
 
 void build_two_vortex_stencils(int N, double x0, double x1, std::vector<double>& q2, std::vector<double>& q1) {
-  convection_stencils(N, x0, x1, 3, q2);
-  convection_stencils(N, x0, x1, 2, q1);
+  convection_stencils(N, x0, x1, 3, nullptr, q2);
+  convection_stencils(N, x0, x1, 2, nullptr, q1);
+}
+
+void build_nodal_wind_stencils(int N, double x0, double x1, const double* wind, std::vector<double>& q2,
+                               std::vector<double>& q1) {
+  convection_stencils(N, x0, x1, 3, wind, q2);
+  convection_stencils(N, x0, x1, 2, wind, q1);
 }
 
 void build_level_tables(int N, double x0, double x1, std::vector<double>& q2, std::vector<double>& q1) {

@@ -12,4 +12,8 @@ void build_b_tables(int N, double x0, double x1, std::vector<double>& bt);
 // (ix, iy) to (ix+dx-2, iy+dy-2)), q1 [(N+1)^2][9] likewise with offsets -1..1.
 // The wind is taken at the 4 x 4 Gauss points of each element.
 void build_two_vortex_stencils(int N, double x0, double x1, std::vector<double>& q2, std::vector<double>& q1);
+// The same for a caller-given wind: the Q2 interpolant of nodal values
+// wind[2][(2N+1)^2] on this level's grid, taken at the same Gauss points.
+void build_nodal_wind_stencils(int N, double x0, double x1, const double* wind, std::vector<double>& q2,
+                               std::vector<double>& q1);
 }  // namespace pint

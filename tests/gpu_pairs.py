@@ -16,21 +16,29 @@ KP_FP64_TOL = 4e-12
 
 
 def make_pair(kind, level, K, beta=1e-2, nu=1e-2, prec=0, T=1.0, **kw):
-    """kind: "stokes" ([0,1]^2), "oseen" (recirculating wind) or "oseen-2v"
-    (the Sec. 5.2 two-vortex wind), both Oseen kinds on [-1,1]^2."""
+    """kind: "stokes" ([0,1]^2), "oseen" (recirculating wind), "oseen-2v"
+    (the Sec. 5.2 two-vortex wind) or "oseen-nodal" (a caller-given nodal
+    wind: the two-vortex wind's values at the Q2 nodes), the Oseen kinds on
+    [-1,1]^2."""
     import torch
+    from oracle import fem
     tau = T / (K + 1)
+    nodal = None
     if kind == "stokes":
         x0, x1, wind, wcode = 0.0, 1.0, None, 0
     elif kind == "oseen-2v":
         x0, x1, wind, wcode = -1.0, 1.0, "two_vortex", 2
+    elif kind == "oseen-nodal":
+        X, Y = fem.Grid(2 ** level, -1.0, 1.0).q2_coords()
+        nodal = np.stack(fem.two_vortex_wind(X, Y))
+        x0, x1, wind, wcode = -1.0, 1.0, ("nodal", nodal), 3
     else:
         x0, x1, wind, wcode = -1.0, 1.0, "recirc", 1
     kind = "stokes" if kind == "stokes" else "oseen"
     P = kkt.Problem(kind, level, K, tau, beta, nu, x0, x1, wind)
     params = binding.default_params(kind=0 if kind == "stokes" else 1, level=level, n_t=K, tau=tau, beta=beta,
                                     nu=nu, x0=x0, x1=x1, wind=wcode, prec=prec, **kw)
-    G = binding.Problem(params, stream=torch.cuda.current_stream().cuda_stream)
+    G = binding.Problem(params, stream=torch.cuda.current_stream().cuda_stream, wind=nodal)
     return P, G
 
 

@@ -3,6 +3,8 @@ function include/pint.h declares; argument validation needs no GPU."""
 import ctypes
 import os
 
+import numpy as np
+
 import pytest
 
 from paper_2405_18964_gb300 import binding
@@ -51,9 +53,23 @@ def test_default_params_and_argument_validation():
         bad = binding.default_params(kind=1, wind=wind, x0=0.0, x1=1.0)
         assert binding.lib().pint_create(ctypes.byref(bad), None, ctypes.byref(h)) == 1
         assert b"[-1,1]" in binding.lib().pint_last_error(None)
-    bad = binding.default_params(kind=1, wind=3, x0=-1.0, x1=1.0)
+    bad = binding.default_params(kind=1, wind=4, x0=-1.0, x1=1.0)
     assert binding.lib().pint_create(ctypes.byref(bad), None, ctypes.byref(h)) == 1
     assert b"wind" in binding.lib().pint_last_error(None)
+    # a nodal wind goes through pint_create_wind, with finite values, on any domain
+    nodal = binding.default_params(kind=1, wind=3, level=2, x0=0.0, x1=1.0)
+    assert binding.lib().pint_create(ctypes.byref(nodal), None, ctypes.byref(h)) == 1
+    assert b"pint_create_wind" in binding.lib().pint_last_error(None)
+    w = np.zeros(2 * 81)
+    wp = w.ctypes.data_as(ctypes.c_void_p)
+    assert binding.lib().pint_create_wind(ctypes.byref(bad), wp, None, ctypes.byref(h)) == 1
+    assert binding.lib().pint_create_wind(ctypes.byref(nodal), None, None, ctypes.byref(h)) == 1
+    w[5] = np.nan
+    assert binding.lib().pint_create_wind(ctypes.byref(nodal), wp, None, ctypes.byref(h)) == 5
+    recirc = binding.default_params(kind=1, wind=1, level=2, x0=-1.0, x1=1.0)
+    w[5] = 0.0
+    assert binding.lib().pint_create_wind(ctypes.byref(recirc), wp, None, ctypes.byref(h)) == 1
+    assert b"PINT_WIND_NODAL" in binding.lib().pint_last_error(None)
     bad = binding.default_params(prec=0, dft_mode=2)          # tensor-core DFT needs FP32
     assert binding.lib().pint_create(ctypes.byref(bad), None, ctypes.byref(h)) == 1
     assert b"dft" in binding.lib().pint_last_error(None).lower()

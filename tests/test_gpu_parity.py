@@ -18,7 +18,8 @@ pytestmark = pytest.mark.gpu
 if not torch.cuda.is_available():
     pytest.skip("no CUDA device", allow_module_level=True)
 
-KINDS = [("stokes", 3, 8), ("oseen", 3, 8), ("stokes", 2, 5), ("oseen", 4, 4), ("oseen-2v", 3, 8)]
+KINDS = [("stokes", 3, 8), ("oseen", 3, 8), ("stokes", 2, 5), ("oseen", 4, 4), ("oseen-2v", 3, 8),
+         ("oseen-nodal", 3, 8)]
 IDS = [f"{k}-L{l}-K{K}" for k, l, K in KINDS]
 
 
