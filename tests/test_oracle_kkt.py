@@ -177,11 +177,14 @@ def test_hat_Pj_eigenvalue_bounds(j):
     assert ev.max() <= g["hat_P_j_abs_upper"] + 1e-10
 
 
+@pytest.mark.parametrize("wind", ["recirc", "two_vortex"])
 @pytest.mark.parametrize("j", [0, 1, 3])
-def test_pearson_wathen_bounds_complex(j):
-    """lambda(S^^{-1} S) in [1/2, 1] for the Oseen (1,1) block (Sec. 2.3, Sec. 4)."""
+def test_pearson_wathen_bounds_complex(j, wind):
+    """lambda(S^^{-1} S) in [1/2, 1] for the Oseen (1,1) block (Sec. 2.3, Sec. 4);
+    the bound needs L + L^T = 2 nu K (skew N), which the skew-symmetric form
+    of the two-vortex wind keeps."""
     g = paper_bounds()
-    P = oseen(2, 6, beta=1e-3, tau=0.2)
+    P = oseen(2, 6, beta=1e-3, tau=0.2, wind=wind)
     t, b = P.tau, P.beta
     d = P.d(j)
     M = P.Mv.toarray()
