@@ -48,8 +48,9 @@ def _forward(P, u, v0=None):
     return v
 
 
-@pytest.mark.parametrize("P", [stokes(1, 3), stokes(2, 5), oseen(1, 4), oseen(2, 3)],
-                         ids=lambda P: f"{P.kind}-L{P.level}-K{P.K}")
+@pytest.mark.parametrize("P", [stokes(1, 3), stokes(2, 5), oseen(1, 4), oseen(2, 3),
+                               oseen(2, 3, wind="two_vortex")],
+                         ids=lambda P: f"{P.kind}-{P.wind}-L{P.level}-K{P.K}")
 def test_kkt_solution_minimises_the_control_objective(P):
     """The solution of A x = b must be the minimiser of J subject to the
     discrete state equation, with u = lambda / beta (Sec. 2.1-2.2): this pins
