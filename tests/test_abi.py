@@ -78,3 +78,16 @@ def test_default_params_and_argument_validation():
     bad = binding.default_params(dft_mode=7)
     assert binding.lib().pint_create(ctypes.byref(bad), None, ctypes.byref(h)) == 1
     assert binding.lib().pint_destroy(None) == 0
+
+
+def test_device_estimate_counts_the_convection_tables():
+    """pint_estimate_device_bytes (host only): Oseen with a wind needs the
+    per-level convection stencils, the non-polynomial winds also their FP64
+    node-order copies; invalid parameters give 0."""
+    est = lambda **kw: binding.estimate_device_bytes(binding.default_params(**kw))
+    base = dict(kind=1, level=6, n_t=64, x0=-1.0, x1=1.0, prec=1)
+    none, recirc, two, nodal = (est(wind=w, **base) for w in (0, 1, 2, 3))
+    assert 0 < none < recirc < two == nodal
+    n2 = 2 * 64 + 1
+    assert two - recirc >= n2 * n2 * 25 * 8          # at least the finest FP64 stencil table
+    assert est(level=0) == 0
