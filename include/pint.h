@@ -371,6 +371,18 @@ size_t pint_autotune_report(char* buf, size_t len);
 typedef enum { PINT_INJECT_DFT_STALL = 1 } pint_inject;
 pint_status pint_debug_inject(pint_handle h, int what);
 
+/* Host only, no CUDA call: the FP64 convection stencils that pint_create
+ * builds for p->wind = PINT_WIND_TWO_VORTEX or PINT_WIND_NODAL on multigrid
+ * level l (0 = finest, grids of N / 2^l elements), in node order:
+ * q2_out[(2n+1)^2][25] (entry dy*5+dx couples node (ix, iy) to
+ * (ix+dx-2, iy+dy-2)), q1_out[(n+1)^2][9] likewise with offsets -1..1, where
+ * n = N / 2^l; either output may be NULL.  wind_host: the finest-grid nodal
+ * wind for PINT_WIND_NODAL (as in pint_create_wind), else NULL.
+ * PINT_ERR_ARG for invalid parameters, another wind or l outside
+ * [0, level). */
+pint_status pint_convection_stencils(const pint_params* p, const double* wind_host, int l, double* q2_out,
+                                     double* q1_out);
+
 const char* pint_last_error(pint_handle h);
 
 #ifdef __cplusplus

@@ -93,6 +93,7 @@ _SIGS = {
     "pint_profile_enable": (ctypes.c_int, [_P, ctypes.c_uint]),
     "pint_profile_read": (ctypes.c_int, [_P, ctypes.POINTER(Profile)]),
     "pint_debug_inject": (ctypes.c_int, [_P, ctypes.c_int]),
+    "pint_convection_stencils": (ctypes.c_int, [ctypes.POINTER(Params), _P, ctypes.c_int, _P, _P]),
     "pint_estimate_device_bytes": (ctypes.c_size_t, [ctypes.POINTER(Params)]),
     "pint_autotune": (None, [ctypes.c_int]),
     "pint_autotune_report": (ctypes.c_size_t, [ctypes.c_char_p, ctypes.c_size_t]),
@@ -305,6 +306,20 @@ class Problem:
     def component_apply(self, which, j, x, y):
         w = COMPONENT[which] if isinstance(which, str) else int(which)
         _check(lib().pint_component_apply(self.h, w, j, _dptr(x, "complex128"), _dptr(y, "complex128")), self.h)
+
+
+def convection_stencils(params, level_index=0, wind=None):
+    """(q2, q1): the FP64 node-order convection stencils the library builds
+    for the two-vortex or nodal wind on one multigrid level (host only)."""
+    n = 2 ** (params.level - level_index)
+    q2 = np.zeros(((2 * n + 1) ** 2, 25))
+    q1 = np.zeros(((n + 1) ** 2, 9))
+    n2 = 2 * 2 ** params.level + 1
+    w = _hptr(wind, 2 * n2 * n2)
+    wp = w.ctypes.data_as(ctypes.c_void_p) if w is not None else None
+    _check(lib().pint_convection_stencils(ctypes.byref(params), wp, level_index,
+                                          q2.ctypes.data_as(ctypes.c_void_p), q1.ctypes.data_as(ctypes.c_void_p)))
+    return q2, q1
 
 
 def autotune(on=True):

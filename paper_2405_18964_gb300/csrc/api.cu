@@ -673,6 +673,24 @@ MGLayout make_layout(int nlev, int N, int space) {
   return L;
 }
 
+// Convection stencils of the two-vortex or nodal wind on level l of p's grid
+// hierarchy (the nodal wind injected from the finest grid).
+void level_convection_stencils(const pint_params& p, const double* wind, int l, std::vector<double>& q2,
+                               std::vector<double>& q1) {
+  const int N = 1 << p.level;
+  if (p.wind == PINT_WIND_NODAL) {
+    const int nf = 2 * N + 1, nl = 2 * (N >> l) + 1, r = 1 << l;
+    std::vector<double> wl(2 * (size_t)nl * nl);
+    for (int comp = 0; comp < 2; ++comp)
+      for (int iy = 0; iy < nl; ++iy)
+        for (int ix = 0; ix < nl; ++ix)
+          wl[((size_t)comp * nl + iy) * nl + ix] = wind[((size_t)comp * nf + (size_t)iy * r) * nf + (size_t)ix * r];
+    build_nodal_wind_stencils(N >> l, p.x0, p.x1, wl.data(), q2, q1);
+  } else {
+    build_two_vortex_stencils(N >> l, p.x0, p.x1, q2, q1);
+  }
+}
+
 pint_status build(pint_ctx* c) {
   const pint_params& p = c->p;
   c->N = 1 << p.level;
@@ -736,18 +754,7 @@ pint_status build(pint_ctx* c) {
   if (c->gwind)
     for (int l = 0; l < c->nlev; ++l) {
       std::vector<double> q2, q1;
-      if (p.wind == PINT_WIND_NODAL) {
-        const int nf = 2 * N + 1, nl = 2 * (N >> l) + 1, r = 1 << l;
-        std::vector<double> wl(2 * (size_t)nl * nl);
-        for (int comp = 0; comp < 2; ++comp)
-          for (int iy = 0; iy < nl; ++iy)
-            for (int ix = 0; ix < nl; ++ix)
-              wl[((size_t)comp * nl + iy) * nl + ix] =
-                  c->wind_nodal[((size_t)comp * nf + (size_t)iy * r) * nf + (size_t)ix * r];
-        build_nodal_wind_stencils(N >> l, p.x0, p.x1, wl.data(), q2, q1);
-      } else {
-        build_two_vortex_stencils(N >> l, p.x0, p.x1, q2, q1);
-      }
+      level_convection_stencils(p, c->wind_nodal.data(), l, q2, q1);
       if (!c->upload(&c->nst64[l], q2) || (l == 0 && !c->upload(&c->npst64, q1)))
         return c->fail(PINT_ERR_OOM, "device allocation failed (convection stencils)");
     }
@@ -1270,6 +1277,28 @@ pint_status pint_create_wind(const pint_params* p, const double* wind_host, void
     return PINT_ERR_ARG;
   }
   return create_impl(p, wind_host, stream, out);
+}
+
+pint_status pint_convection_stencils(const pint_params* p, const double* wind_host, int l, double* q2_out,
+                                     double* q1_out) {
+  std::string why;
+  if (!valid_params(p, why)) {
+    g_err = why;
+    return PINT_ERR_ARG;
+  }
+  if (p->wind != PINT_WIND_TWO_VORTEX && p->wind != PINT_WIND_NODAL) {
+    g_err = "stencils exist for PINT_WIND_TWO_VORTEX and PINT_WIND_NODAL only";
+    return PINT_ERR_ARG;
+  }
+  if ((p->wind == PINT_WIND_NODAL) != (wind_host != nullptr) || l < 0 || l >= p->level) {
+    g_err = "wind_host must be given exactly for PINT_WIND_NODAL, and 0 <= l < level";
+    return PINT_ERR_ARG;
+  }
+  std::vector<double> q2, q1;
+  level_convection_stencils(*p, wind_host, l, q2, q1);
+  if (q2_out) std::memcpy(q2_out, q2.data(), q2.size() * sizeof(double));
+  if (q1_out) std::memcpy(q1_out, q1.data(), q1.size() * sizeof(double));
+  return PINT_OK;
 }
 
 pint_status pint_destroy(pint_handle h) {

@@ -91,3 +91,40 @@ def test_device_estimate_counts_the_convection_tables():
     n2 = 2 * 64 + 1
     assert two - recirc >= n2 * n2 * 25 * 8          # at least the finest FP64 stencil table
     assert est(level=0) == 0
+
+
+def _band_to_dense(st, n, hw):
+    bw = 2 * hw + 1
+    D = np.zeros((n * n, n * n))
+    for i in range(n * n):
+        ix, iy = i % n, i // n
+        for k in range(bw * bw):
+            jx, jy = ix + k % bw - hw, iy + k // bw - hw
+            if 0 <= jx < n and 0 <= jy < n:
+                D[i, jy * n + jx] = st[i, k]
+    return D
+
+
+@pytest.mark.parametrize("wind", [2, 3])
+def test_host_convection_stencils_match_the_oracle(wind):
+    """The FP64 convection stencils the library integrates on the host (two-
+    vortex wind; a random nodal wind, injected to the coarse level) equal the
+    oracle's skew-symmetric convection matrices on every level, Q2 and Q1."""
+    if not os.path.exists(binding.LIB_PATH):
+        pytest.skip("libpint.so not built (run __graft_entry__.build())")
+    from oracle import fem
+    level = 3
+    N = 2 ** level
+    W = np.random.default_rng(4).standard_normal((2, (2 * N + 1) ** 2)) if wind == 3 else None
+    p = binding.default_params(kind=1, level=level, wind=wind, x0=-1.0, x1=1.0)
+    name = ("nodal", W) if wind == 3 else "two_vortex"
+    for l in range(level):
+        n = N >> l
+        q2, q1 = binding.convection_stencils(p, l, W)
+        wf, skew = fem.wind_by_name(name, n, -1.0, 1.0)
+        o = fem.assemble(n, -1.0, 1.0, wf, skew=skew)
+        for st, A, m, hw in ((q2, o.N, 2 * n + 1, 2), (q1, o.Np, n + 1, 1)):
+            ref = A.toarray()
+            assert np.abs(_band_to_dense(st, m, hw) - ref).max() <= 1e-14 * np.abs(ref).max()
+    with pytest.raises(binding.PintError):
+        binding.convection_stencils(binding.default_params(kind=1, level=level, wind=1, x0=-1.0, x1=1.0))
