@@ -8,10 +8,11 @@ assembles sparse matrices from a generic Lagrange-basis element loop and
 follows the paper's formulas step by step.
 
 Modules
-  fem      Q2-Q1 Taylor-Hood operators on a uniform square grid (Sec. 2.2)
-  kkt      all-at-once KKT matrix (Eq. FinalA), right-hand side, the
-           block-circulant P_C and its exact FFT-diagonalised inverse
-           (Sec. 3.1), FGMRES (Sec. 3.4)
+  fem      Q2-Q1 Taylor-Hood operators on a uniform square grid (Sec. 2.2),
+           the winds (recirculating, the Sec. 5.2 two-vortex wind, nodal)
+  kkt      all-at-once KKT matrix (Eq. FinalA), right-hand sides (zero and
+           prescribed boundary velocity, Sec. 5), the block-circulant P_C and
+           its exact FFT-diagonalised inverse (Sec. 3.1), FGMRES (Sec. 3.4)
   inexact  Chebyshev semi-iteration, geometric multigrid with multicolour
            SOR, the Stokes transform G_j = T^l Z_j T^r (Eq. GJTransformation),
            the commutator preconditioner P~_j, inexact Uzawa and Algorithm 3
@@ -20,8 +21,8 @@ Modules
            (Dirichlet-eliminated, pressure-pinned) vectors used here
 
 Parity status: every function is pinned by a `-m "not gpu"` test against a
-closed form, an invariant, a brute-force solve or a bound printed in the
-paper, except the inexact nested preconditioners (Chebyshev / MG / Uzawa
+closed form (among them the Sec. 5.1 exact solution), an invariant, a
+brute-force solve or a bound printed in the paper, except the inexact nested preconditioners (Chebyshev / MG / Uzawa
 combinations), whose intermediate values the paper never prints: those are
 pinned only through convergence to their exact counterparts as iteration
 counts grow ("parity unpinned" for the exact iterate values; see

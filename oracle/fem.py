@@ -14,11 +14,17 @@ space (Sec. 2.2, "P2-P1 ... and Q2-Q1"); the matrices named there are
                                             commutator argument)
 
 Everything is assembled by a plain element loop with a generic Lagrange
-basis evaluated at 4x4 Gauss points (exact for every integrand here: the
-recirculating wind is polynomial).  Readings where the paper is silent:
-velocity boundary nodes carry homogeneous Dirichlet conditions and are
-eliminated; the pressure is pinned at the lower-left Q1 node (index 0), "one
+basis evaluated at 4x4 Gauss points (exact for every integrand of the
+polynomial recirculating wind).  Readings where the paper is silent:
+velocity boundary nodes carry Dirichlet conditions and are eliminated (their
+values, when not zero, enter the right-hand side: `kkt.Problem.rhs_dirichlet`);
+the pressure is pinned at the lower-left Q1 node (index 0), "one
 pre-defined point" (Sec. 2.2); K_p and N_p use natural boundary conditions.
+Winds: the recirculating wind; the Sec. 5.2 two-vortex wind, whose printed
+second branch is read as the divergence-free vortex about (-1/2, 0); a
+caller-given nodal wind (its Q2 interpolant, injected to coarser grids).
+The last two are not polynomials, so their convection matrices are taken in
+the skew-symmetric form (N - N^T)/2 (`wind_by_name`).
 """
 from dataclasses import dataclass
 

@@ -18,6 +18,10 @@ What it follows
     inverse FFT.  The frequency block is Eq. SubBlockG.
   * Sec. 3.4: flexible GMRES (Saad 1993) as the outer solver.
 
+  * Sec. 5 problems (`rhs_dirichlet`): the prescribed boundary velocity is
+    a known part of the state, moved to the right-hand side; the data are
+    nodal interpolants on the whole grid, loaded with the full mass rows.
+
 Readings (the paper is ambiguous here):
   R1  K = n_t time blocks, block k <-> t_k = k tau for state and adjoint;
       lambda_{K+1} = 0, v_0 enters the right-hand side.  tau is an input.
