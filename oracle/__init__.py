@@ -22,9 +22,9 @@ Modules
 
 Parity status: every function is pinned by a `-m "not gpu"` test against a
 closed form (among them the Sec. 5.1 exact solution), an invariant, a
-brute-force solve or a bound printed in the paper, except the inexact nested preconditioners (Chebyshev / MG / Uzawa
-combinations), whose intermediate values the paper never prints: those are
-pinned only through convergence to their exact counterparts as iteration
-counts grow ("parity unpinned" for the exact iterate values; see
-``inexact``'s header).
+brute-force solve or a bound printed in the paper, except the inexact
+nested preconditioners (Chebyshev / MG / Uzawa combinations), whose
+intermediate values the paper never prints: those are pinned only through
+convergence to their exact counterparts as iteration counts grow ("parity
+unpinned" for the exact iterate values; see ``inexact``'s header).
 """
