@@ -333,8 +333,11 @@ typedef struct {
 /* Start the worker threads.  PINT_ERR_ARG for max_active outside [1, 64]. */
 pint_status pint_server_create(const pint_server_params* sp, pint_server* out);
 /* Queue a request.  vd (host, [n_t][2][n_s]) is copied, as are the optional
- * f ([n_t][2][n_s]) and v0 ([2][n_s]).  PINT_ERR_ARG for invalid params,
- * PINT_ERR_OOM if the estimate exceeds the whole budget. */
+ * f ([n_t][2][n_s]) and v0 ([2][n_s]); the data are those of pint_set_data
+ * (zero boundary velocity), and a request's handle is made by pint_create
+ * (so PINT_WIND_NODAL is refused by the worker, which reports the failure
+ * through pint_server_wait).  PINT_ERR_ARG for invalid params, PINT_ERR_OOM
+ * if the estimate exceeds the whole budget. */
 pint_status pint_server_submit(pint_server s, const pint_params* p, const double* vd, const double* f,
                                const double* v0, long long* id);
 /* Block until request id completes; copy its solution (host, kkt_len
