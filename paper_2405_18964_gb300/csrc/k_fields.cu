@@ -50,7 +50,8 @@ __device__ __forceinline__ void q2_mkn_r(const double* __restrict__ tab, int n2,
 }
 
 // One row of a node-order convection stencil applied to a Q2 field at an
-// interior node (all 25 neighbours exist).
+// interior node.  Offsets that leave the grid (+-2 from a midside node next to
+// the boundary) are clamped; their stencil entries are zero.
 __device__ __forceinline__ double conv_row_r(const double* __restrict__ st, int n2, int ix, int iy,
                                              const double* __restrict__ x) {
   double acc = 0.0;
