@@ -352,3 +352,26 @@ def test_theorems_2_3_eigenvalue_clusters(schur):
     mu = np.abs(np.linalg.eigvals(_hat_preconditioned_operator(P, schur)))
     inside = np.count_nonzero((mu >= a * (1 - 1e-9)) & (mu <= b * (1 + 1e-9)))
     assert inside >= len(mu) - 4 * P.nv, (inside, len(mu), P.nv)
+
+
+def test_damped_sor_rescues_the_convection_dominated_Q0():
+    """The limitation of the recirculating wind at beta >= 1e-2: the Q_0
+    multigrid with Gauss-Seidel smoothing (omega = 1) diverges, more sweeps
+    make it worse (the smoother itself amplifies), and under-relaxed SOR
+    (omega = 0.7) converges.  Q_0 = (tau / sqrt(beta)) M + tau (nu K + N)."""
+    K, beta, nu = 8, 1e-2, 1e-2
+    tau = 1.0 / (K + 1)
+    aM, aK, aN = tau / np.sqrt(beta), tau * nu, tau
+
+    def err(**kw):
+        mg = inexact.Multigrid("q2", 3, -1.0, 1.0, "recirc", aM, aK, aN, **kw)
+        A = mg.levels[0].A
+        rng = np.random.default_rng(0)
+        b = rng.standard_normal(A.shape[0]) + 1j * rng.standard_normal(A.shape[0])
+        xt = spla.spsolve(A.tocsc().astype(complex), b)
+        with np.errstate(all="ignore"):
+            return np.linalg.norm(mg.solve(b, 4) - xt) / np.linalg.norm(xt)
+
+    e1, e_more, e07 = err(), err(pre=4, post=4), err(omega=0.7)
+    assert e1 > 1.0 and e_more > e1
+    assert e07 < 0.1
