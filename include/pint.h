@@ -172,6 +172,8 @@ pint_status pint_create_wind(const pint_params* p, const double* wind_host, void
 /* Frees everything the handle owns.  Accepts NULL. */
 pint_status pint_destroy(pint_handle h);
 
+/* Sizes of the handle's vectors and its device workspace (host struct,
+ * caller-owned).  PINT_ERR_ARG for a NULL argument. */
 pint_status pint_get_sizes(pint_handle h, pint_sizes* s);
 
 /* Problem data (Sec. 2.2 backward-Euler equations): builds the right-hand
@@ -202,21 +204,30 @@ pint_status pint_set_data(pint_handle h, const double* vd_host, const double* f_
 pint_status pint_set_data_dirichlet(pint_handle h, const double* vd_host, const double* f_host,
                                     const double* v0_host, const double* g_host);
 
-/* Copy the assembled right-hand side b (KKT vector) to b_dev. */
+/* Copy the assembled right-hand side b (KKT vector) to b_dev (caller-owned,
+ * n_t * n_blk doubles).  PINT_ERR_STATE before pint_set_data or
+ * pint_set_data_dirichlet. */
 pint_status pint_get_rhs(pint_handle h, double* b_dev);
 
 /* y = A x with A of Eq. FinalA, FP64, matrix-free.  x_dev, y_dev: KKT
- * vectors (must not overlap). */
+ * vectors (must not overlap); entries of x_dev that are not unknowns are
+ * ignored.  Asynchronous on the handle's stream; PINT_ERR_CUDA if a launch
+ * fails. */
 pint_status pint_kkt_matvec(pint_handle h, const double* x_dev, double* y_dev);
 
 /* z = P^{-1} r: the parallel-in-time preconditioner (Algorithm 1 if
  * params.linear, else Algorithm 2 (Stokes) / the Uzawa variant (Oseen)),
- * in the handle's precision.  r_dev, z_dev: KKT vectors. */
+ * in the handle's precision.  r_dev, z_dev: KKT vectors.  PINT_ERR_TIMEOUT
+ * if a bounded wait of the tensor-core DFT gave up (the handle stays
+ * usable), PINT_ERR_CUDA on launch failure. */
 pint_status pint_apply_preconditioner(pint_handle h, const double* r_dev, double* z_dev);
 
 /* Solve A x = b by FP64 FGMRES(m) with the preconditioner.  x_dev: in =
  * initial guess, out = solution (KKT vector).  info may be NULL.  Returns
- * PINT_ERR_NOT_CONVERGED (with x the last iterate) if outer_maxit is hit. */
+ * PINT_ERR_NOT_CONVERGED (with x the last iterate) if outer_maxit is hit,
+ * PINT_ERR_NONFINITE if a preconditioned Krylov vector is not finite (a
+ * diverging inexact preconditioner), PINT_ERR_TIMEOUT as for
+ * pint_apply_preconditioner, PINT_ERR_STATE before the data are set. */
 pint_status pint_solve(pint_handle h, double* x_dev, pint_solve_info* info);
 
 /* Same as pint_solve with host buffers: copies the initial guess host to
