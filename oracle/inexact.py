@@ -247,9 +247,11 @@ class Settings:
     Chebyshev steps, 6 Uzawa steps, mu = 3/4, inner tolerance 1e-2)."""
 
     def __init__(self, mg_cycles=4, mg_pre=2, mg_post=2, sor_omega=1.0, cheb_steps=10,
-                 uzawa_steps=6, uzawa_mu=0.75, inner_tol=1e-2, inner_maxit=100):
+                 uzawa_steps=6, uzawa_mu=0.75, inner_tol=1e-2, inner_maxit=100, sor_omega_conv=None):
         self.mg_cycles, self.mg_pre, self.mg_post = mg_cycles, mg_pre, mg_post
         self.sor_omega = sor_omega
+        # SOR relaxation of the convection operators Q_j, Q_j^H (default: sor_omega)
+        self.sor_omega_conv = sor_omega if sor_omega_conv is None else sor_omega_conv
         self.cheb_steps = cheb_steps
         self.uzawa_steps, self.uzawa_mu = uzawa_steps, uzawa_mu
         self.inner_tol, self.inner_maxit = inner_tol, inner_maxit
@@ -307,7 +309,7 @@ class OseenBlockPreconditioner:
         aQ = d + t / np.sqrt(b)
         # Q_j = d M + tau (nu K + N) + tau/sqrt(beta) M ; Q_j^H = conj(.) M + tau (nu K + N^T)
         self.mgQ = Multigrid("q2", P.level, P.x0, P.x1, P.wind, aQ, t * P.nu, t,
-                             s.mg_pre, s.mg_post, s.sor_omega)
+                             s.mg_pre, s.mg_post, s.sor_omega_conv)
         self.mgQH = _TransposedMG(P, np.conj(aQ), t * P.nu, t, s)
         self.mgKp = kp_mg if kp_mg is not None else Multigrid(
             "q1", P.level, P.x0, P.x1, None, 0.0, 1.0, 0.0, s.mg_pre, s.mg_post, s.sor_omega)
@@ -375,7 +377,7 @@ class _TransposedMG(Multigrid):
 
     def __init__(self, P, aM, aK, aNT, s):
         self.space = "q2"
-        self.pre, self.post, self.omega = s.mg_pre, s.mg_post, s.sor_omega
+        self.pre, self.post, self.omega = s.mg_pre, s.mg_post, s.sor_omega_conv
         self.levels = []
         for lv in range(P.level, 0, -1):
             N = 2 ** lv

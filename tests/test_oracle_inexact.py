@@ -375,3 +375,18 @@ def test_damped_sor_rescues_the_convection_dominated_Q0():
     e1, e_more, e07 = err(), err(pre=4, post=4), err(omega=0.7)
     assert e1 > 1.0 and e_more > e1
     assert e07 < 0.1
+
+
+def test_convection_only_damping_converges_the_recirculating_wind():
+    """Damping only the SOR of Q_j and Q_j^H (sor_omega_conv), with K_p keeping
+    Gauss-Seidel, is enough: the beta = 1e-2 recirculating-wind problem whose
+    Q_0 multigrid diverges at omega = 1 converges in FGMRES(10)."""
+    P = kkt.Problem("oseen", 3, 4, 0.2, 1e-2, 1e-2, -1.0, 1.0, "recirc")
+    s = inexact.Settings(sor_omega_conv=0.5, inner_maxit=60)
+    pc = inexact.PinTPreconditioner(P, s)
+    blk = pc.block_prec(0)
+    assert blk.mgQ.omega == 0.5 and blk.mgQH.omega == 0.5 and blk.mgKp.omega == 1.0
+    from paper_2405_18964_gb300 import inputs
+    b = P.rhs(inputs.desired_state(P.N, -1.0, 1.0, P.K, P.tau, 1.0, seed=0))
+    x, info = kkt.fgmres(P.kkt_matrix(), b, pc, restart=10, tol=1e-8, maxit=30)
+    assert info["relres"] <= 1e-8 and info["its"] <= 15, info["its"]
