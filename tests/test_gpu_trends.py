@@ -91,7 +91,7 @@ def test_nested_preconditioner_with_the_papers_data(kind):
     """Tables 2-5 with the paper's own problems: Sec. 5.1 data at nu = 1e-2,
     T = 10 (Stokes, 16x16), the Sec. 5.2 lid-driven cavity with its
     two-vortex wind at nu = 1e-2, T = 1 (Oseen, 32x32).  The two-vortex wind
-    is weaker than the recirculating one (|w| <= 1/2), and beta = 1e-2
+    is weaker than the recirculating one (|w| <= 0.51 against 2), and beta = 1e-2
     converges with it."""
     level, T = (4, 10.0) if kind == "stokes" else (5, 1.0)
     betas = (1e-1, 1e-3, 1e-4) if kind == "stokes" else (1e-2, 1e-4, 1e-6)
