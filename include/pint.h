@@ -125,6 +125,10 @@ typedef struct {
   int fixed_inner_its; /* > 0: run exactly this many inner GMRES iterations  */
   int linear;          /* 1: Algorithm 1 (no inner GMRES), 0: Algorithm 2/3  */
   int dft_mode;        /* pint_dft_mode                                      */
+  /* SOR relaxation of the Oseen velocity multigrids on Q_j and Q_j^H (Sec. 4); */
+  /* 0 = sor_omega.  Values below 1 keep those multigrids convergent on the      */
+  /* convection-dominated low-frequency Q_j of large beta.                        */
+  double sor_omega_conv;
 } pint_params;
 
 typedef struct {
@@ -151,7 +155,8 @@ typedef struct {
 size_t pint_estimate_device_bytes(const pint_params* p);
 
 /* Defaults from Sec. 5: FGMRES(30), inner tolerance 1e-2, 4 V-cycles with
- * 2+2 SOR sweeps (omega = 1), 10 Chebyshev steps, 6 Uzawa steps, mu = 3/4,
+ * 2+2 SOR sweeps (omega = 1, also for Q_j: sor_omega_conv = 0), 10
+ * Chebyshev steps, 6 Uzawa steps, mu = 3/4,
  * inner cap 100, outer tolerance 1e-8.  Problem fields are set to a Stokes
  * problem on [0,1]^2 with N = 8, n_t = 8, tau = 1/9, beta = 1e-2, nu = 1e-2. */
 void pint_default_params(pint_params* p);
@@ -279,8 +284,14 @@ pint_status pint_component_apply(pint_handle h, int which, int j, const double* 
  * bytes needed.  The first call on a device looks up the array's device
  * address (make that first call before any stream capture).  All calls
  * share the array: calls that overlap on the GPU race.  Inputs and outputs
- * as in pint_component_apply (complex FP64, full grid, caller-owned);
- * the device current at the call must be the handle's device. */
+ * as in pint_component_apply (complex FP64, full grid, caller-owned: n_s
+ * values for which = 0..2, n_q for which = 3; the call takes no length, so
+ * shorter buffers are read or written past their end); the device current
+ * at the call must be the handle's device.  Unlike pint_component_apply the
+ * call is asynchronous: it returns with its work queued on the handle's
+ * stream, and in_dev and out_dev must stay valid (and out_dev unread) until
+ * that stream is synchronised.  The multigrid autotuner is not consulted
+ * (its bookkeeping would allocate): the CTA size is the fixed heuristic. */
 pint_status pint_mg_apply_noalloc(pint_handle h, int which, int j, const double* in_dev, double* out_dev);
 
 /* ---- tracing ------------------------------------------------------------
@@ -299,13 +310,28 @@ enum {
   PINT_PROF_KKT_MV = 8,     /* FP64 KKT matvec (Eq. FinalA)                    */
   PINT_PROF_OUTER = 9,      /* outer FGMRES vector kernels                     */
   PINT_PROF_OTHER = 10,     /* masking, conversions, right-hand side           */
-  PINT_PROF_CLASSES = 11
+  PINT_PROF_APPLY = 11,     /* whole preconditioner applies (timing only: the
+                             * events bracket every kernel of an apply, both
+                             * streams; its launches are counted in the
+                             * classes above)                                  */
+  PINT_PROF_CLASSES = 12
 };
 
 typedef struct {
   long long launches[PINT_PROF_CLASSES]; /* kernels launched since the reset    */
   long long timed[PINT_PROF_CLASSES];    /* launches covered by event timing    */
   double ms[PINT_PROF_CLASSES];          /* summed event time of timed launches */
+  /* Algorithmic bytes of the launches since the reset, counted whether or not
+   * the class is timed: the compulsory traffic of each kernel's work, every
+   * operand read once and every result written once (b_w bytes per real word
+   * of the kernel's precision, c = 2 for complex data, n nodes of a field):
+   * multigrid (4 (pre + post) + 8) n c b_w per V-cycle and field, Chebyshev
+   * 5 n c b_w per step and field, block matvec 2 n_blk c b_w per frequency,
+   * Gram-Schmidt (4 i + 8) n_blk c b_w at inner step i, time DFT
+   * 8 n_t n_blk + J n_blk c b_w per transform, KKT matvec 16 n_t n_blk,
+   * operator combinations their fields read and written once; only the
+   * frequencies still active in the inner GMRES are counted. */
+  double bytes[PINT_PROF_CLASSES];
 } pint_profile;
 
 /* Reset the counters and select the timed classes (bit i = class i). */

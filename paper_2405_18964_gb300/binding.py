@@ -33,7 +33,7 @@ class Params(ctypes.Structure):
                 ("inner_maxit", ctypes.c_int), ("mg_cycles", ctypes.c_int), ("mg_pre", ctypes.c_int),
                 ("mg_post", ctypes.c_int), ("cheb_steps", ctypes.c_int), ("uzawa_steps", ctypes.c_int),
                 ("uzawa_mu", ctypes.c_double), ("sor_omega", ctypes.c_double), ("fixed_inner_its", ctypes.c_int),
-                ("linear", ctypes.c_int), ("dft_mode", ctypes.c_int)]
+                ("linear", ctypes.c_int), ("dft_mode", ctypes.c_int), ("sor_omega_conv", ctypes.c_double)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -51,12 +51,14 @@ class Sizes(ctypes.Structure):
 
 
 PROF_CLASSES = ["mg_q2", "mg_q1", "cheb", "dft_fwd", "dft_inv", "block_mv", "combo", "inner", "kkt_mv", "outer",
-                "other"]
+                "other", "apply"]
+# kernel classes whose launches make up a preconditioner apply
+APPLY_CLASSES = ["mg_q2", "mg_q1", "cheb", "dft_fwd", "dft_inv", "block_mv", "combo", "inner"]
 
 
 class Profile(ctypes.Structure):
-    _fields_ = [("launches", ctypes.c_longlong * 11), ("timed", ctypes.c_longlong * 11),
-                ("ms", ctypes.c_double * 11)]
+    _fields_ = [("launches", ctypes.c_longlong * 12), ("timed", ctypes.c_longlong * 12),
+                ("ms", ctypes.c_double * 12), ("bytes", ctypes.c_double * 12)]
 
 
 _lib = None
@@ -285,9 +287,12 @@ class Problem:
         _check(lib().pint_debug_inject(self.h, int(what)), self.h)
 
     def mg_apply_noalloc(self, which, j, x, y):
-        """Multigrid on one field with the library's fixed scratch array (no allocation)."""
+        """Multigrid on one field with the library's fixed scratch array (no
+        allocation).  Asynchronous on the handle's stream: x and y must stay
+        valid, and y unread, until that stream is synchronised."""
         w = COMPONENT[which] if isinstance(which, str) else int(which)
-        _check(lib().pint_mg_apply_noalloc(self.h, w, j, _dptr(x, "complex128"), _dptr(y, "complex128")),
+        n = component_len(self.sizes, w)
+        _check(lib().pint_mg_apply_noalloc(self.h, w, j, _dptr(x, "complex128", n), _dptr(y, "complex128", n)),
                self.h)
 
     def profile_enable(self, classes=()):
@@ -300,12 +305,24 @@ class Problem:
     def profile_read(self):
         p = Profile()
         _check(lib().pint_profile_read(self.h, ctypes.byref(p)), self.h)
-        return {c: {"launches": p.launches[i], "timed": p.timed[i], "ms": p.ms[i]}
+        return {c: {"launches": p.launches[i], "timed": p.timed[i], "ms": p.ms[i], "bytes": p.bytes[i]}
                 for i, c in enumerate(PROF_CLASSES)}
 
     def component_apply(self, which, j, x, y):
         w = COMPONENT[which] if isinstance(which, str) else int(which)
-        _check(lib().pint_component_apply(self.h, w, j, _dptr(x, "complex128"), _dptr(y, "complex128")), self.h)
+        n = component_len(self.sizes, w)
+        _check(lib().pint_component_apply(self.h, w, j, _dptr(x, "complex128", n), _dptr(y, "complex128", n)),
+               self.h)
+
+
+def component_len(sizes, which):
+    """Complex values of one component's input and output field: n_q for the
+    pressure operators (3, 5), n_blk for a whole frequency block (6), else n_s."""
+    if which in (3, 5):
+        return int(sizes.n_q)
+    if which == 6:
+        return int(sizes.n_blk)
+    return int(sizes.n_s)
 
 
 def convection_stencils(params, level_index=0, wind=None):

@@ -70,6 +70,8 @@ struct Engine {
                                                               : 0;
   }
   int c_J() const;
+  // fraction of the frequencies whose work a masked launch does
+  double afrac(const int* active) const;
   void mg(int space, bool conv, const FieldJob* jobs, int njobs, cpx<T>* xb, const cpx<T>* bb, const int* active,
           int fields_per_job = 2, cudaStream_t stream = nullptr, cpx<T>* ws = nullptr);
   void cheb(int space, const FieldJob* jobs, int njobs, cpx<T>* xb, const cpx<T>* bb, const int* active,
@@ -87,6 +89,7 @@ struct pint_ctx {
   int N = 0, K = 0, J = 0, nlev = 0, m_in = 0;
   Slots s{};
   bool oseen = false, conv = false, fp32 = false;
+  double omega_conv = 1.0;                // SOR relaxation of the Q_j, Q_j^H multigrids (Oseen)
   bool gwind = false;                     // conv by node stencils (two-vortex or nodal wind), not separable
   std::vector<double> wind_nodal;         // PINT_WIND_NODAL: [2][n_s] values at the finest Q2 nodes
   double* nst64[PINT_MAXLEV] = {};        // node-order FP64 Q2 convection stencils per level (gwind)
@@ -137,6 +140,8 @@ struct pint_ctx {
   long long prof_launch[PINT_PROF_CLASSES] = {};
   long long prof_timed[PINT_PROF_CLASSES] = {};
   double prof_ms[PINT_PROF_CLASSES] = {};
+  double prof_bytes[PINT_PROF_CLASSES] = {};  // algorithmic bytes (pint.h, pint_profile)
+  void add_bytes(int cls, double b) { prof_bytes[cls] += b; }
   struct Pend {
     int cls;
     cudaEvent_t a, b;
@@ -206,6 +211,20 @@ template <class T>
 int Engine<T>::c_J() const {
   return c->J;
 }
+template <class T>
+double Engine<T>::afrac(const int* active) const {
+  return active && active_freqs > 0 ? (double)active_freqs / c->J : 1.0;
+}
+
+// algorithmic bytes of operator combinations: every row's operand fields
+// read once and its output written once, per (active) frequency
+template <class T>
+static double combo_bytes(const Engine<T>& e, const ComboArgs<T>& a, const int* active) {
+  const double len = a.space == 2 ? (double)e.c->s.ns : (double)e.c->s.nq;
+  double f = 0;
+  for (int r = 0; r < a.nrows; ++r) f += a.rows[r].nt + a.rows[r].has_z + 1;
+  return f * len * 2 * sizeof(T) * e.c->J * e.afrac(active);
+}
 
 // RAII scope around the launches of one kernel class: counts nk kernels and,
 // if the class is being timed, records a CUDA event pair on the stream.
@@ -273,11 +292,19 @@ void Engine<T>::mg(int space, bool conv, const FieldJob* jobs, int njobs, cpx<T>
   L.cycles = c->p.mg_cycles;
   L.pre = c->p.mg_pre;
   L.post = c->p.mg_post;
-  L.omega = c->p.sor_omega;
+  L.omega = c->oseen && space == 2 ? c->omega_conv : c->p.sor_omega;
   L.space = space;
   L.conv = conv;
   L.active_jobs = active_jobs(njobs, active);
+  // single-field launches come from the diagnostic component entry points
+  // only: fixed CTA size, no tuner entry
+  L.no_tune = njobs == 1;
   cudaStream_t st = stream ? stream : c->st;
+  {
+    const double n = space == 2 ? (double)c->s.ns : (double)c->s.nq;
+    c->add_bytes(space == 2 ? PINT_PROF_MG_Q2 : PINT_PROF_MG_Q1,
+                 njobs * afrac(active) * (4.0 * (L.pre + L.post) + 8.0) * n * 2 * sizeof(T) * L.cycles);
+  }
   PROF_ON(c, space == 2 ? PINT_PROF_MG_Q2 : PINT_PROF_MG_Q1, 1, st);
   launch_mg<T>(L, st);
 }
@@ -301,6 +328,8 @@ void Engine<T>::cheb(int space, const FieldJob* jobs, int njobs, cpx<T>* xb, con
   L.lmax = space == 2 ? Q2_LMAX : Q1_LMAX;
   L.space = space;
   L.active_jobs = active_jobs(njobs, active);
+  c->add_bytes(PINT_PROF_CHEB, njobs * afrac(active) * fields_per_job * 5.0 *
+                                   (space == 2 ? (double)c->s.ns : (double)c->s.nq) * 2 * sizeof(T) * L.steps);
   PROF_ON(c, PINT_PROF_CHEB, 1, stream ? stream : c->st);
   launch_cheb<T>(L, stream ? stream : c->st);
 }
@@ -318,6 +347,7 @@ void Engine<T>::block_matvec(const BlkCoef* coef, const cpx<T>* X, cpx<T>* Out, 
   a.active = active;
   a.x = X;
   a.y = Out;
+  c->add_bytes(PINT_PROF_BLOCK_MV, c->J * afrac(active) * 2.0 * c->s.nblk * 2 * sizeof(T));
   PROF(c, PINT_PROF_BLOCK_MV, 2);
   launch_block_matvec<T>(a, c->st);
 }
@@ -341,6 +371,7 @@ void Engine<T>::block_prec(const cpx<T>* U, cpx<T>* Out, const int* active) {
     // S^_j^{-1} = (1 + c1) K_p^{-1} + nu c2 M_p^{-1} on the p and mu blocks
     mg(1, false, c->j_Kp2, 2 * J, T1, U, active, 1, sa, mgws_q1);
     cheb(1, c->j_Mp2, J, T2, U, active, 2, sa);
+    c->add_bytes(PINT_PROF_COMBO, 2 * 3.0 * s.nq * 2 * sizeof(T) * J * afrac(active));
     { PROF_ON(c, PINT_PROF_COMBO, 1, sa); launch_lincomb<T>(J, s.nblk, s.nq, Out, s.p, T1, s.p, c->d_sa, T2, s.p, c->d_sb, active, sa); }
     { PROF_ON(c, PINT_PROF_COMBO, 1, sa); launch_lincomb<T>(J, s.nblk, s.nq, Out, s.mu, T1, s.mu, c->d_sa, T2, s.mu, c->d_sb, active, sa); }
     cudaEventRecord(c->ev_join, sa);
@@ -369,9 +400,11 @@ void Engine<T>::block_prec(const cpx<T>* U, cpx<T>* Out, const int* active) {
     ca.x = Out;
     ca.z = U;
     ca.out = T1;
+    c->add_bytes(PINT_PROF_COMBO, combo_bytes(*this, ca, active));
     { PROF(c, PINT_PROF_COMBO, 1); launch_combo<T>(ca, st); }
     // x1 += (1/tau) M^-1 T1[v]   (M^ = Chebyshev)
     cheb(2, c->j_M2, J, T2, T1, active);
+    c->add_bytes(PINT_PROF_COMBO, 3.0 * lenv * 2 * sizeof(T) * J * afrac(active));
     { PROF(c, PINT_PROF_COMBO, 1); launch_lincomb<T>(J, s.nblk, lenv, Out, s.vx, Out, s.vx, c->d_one, T2, s.vx, c->d_invtau, active, st); }
     // T1[lam] = b2 - (d M + tau L) x1 + tau/beta M x2
     ca.coef = c->d_cuzd;
@@ -380,6 +413,7 @@ void Engine<T>::block_prec(const cpx<T>* U, cpx<T>* Out, const int* active) {
     ca.x = Out;
     ca.z = U;
     ca.out = T1;
+    c->add_bytes(PINT_PROF_COMBO, combo_bytes(*this, ca, active));
     { PROF(c, PINT_PROF_COMBO, 1); launch_combo<T>(ca, st); }
     // S^^{-1} = tau Q^{-H} M Q^{-1}
     mg(2, c->conv, c->j_Q2, 2 * J, T2, T1, active, 1);
@@ -390,9 +424,11 @@ void Engine<T>::block_prec(const cpx<T>* U, cpx<T>* Out, const int* active) {
     ca.x = T2;
     ca.z = nullptr;
     ca.out = T3;
+    c->add_bytes(PINT_PROF_COMBO, combo_bytes(*this, ca, active));
     { PROF(c, PINT_PROF_COMBO, 1); launch_combo<T>(ca, st); }
     mg(2, c->conv, c->j_QH2, 2 * J, T1, T3, active, 1);
     // x2 -= (1/mu) tau Q^{-H} M Q^{-1} (...)
+    c->add_bytes(PINT_PROF_COMBO, 3.0 * lenv * 2 * sizeof(T) * J * afrac(active));
     { PROF(c, PINT_PROF_COMBO, 1); launch_lincomb<T>(J, s.nblk, lenv, Out, s.lx, Out, s.lx, c->d_one, T1, s.lx, c->d_mtaumu, active, st); }
   }
   // ---- Algorithm 3: y34 = -S^_j^{-1} (r34 - tau (B y2; B y1))
@@ -411,6 +447,7 @@ void Engine<T>::block_prec(const cpx<T>* U, cpx<T>* Out, const int* active) {
   br.x = Out;
   br.z = U;
   br.out = T1;
+  c->add_bytes(PINT_PROF_COMBO, 2.0 * (2.0 * s.ns + 2.0 * s.nq) * 2 * sizeof(T) * J * afrac(active));
   {
     PROF(c, PINT_PROF_COMBO, 1);
     launch_bres<T>(br, st);
@@ -435,6 +472,7 @@ void Engine<T>::block_prec(const cpx<T>* U, cpx<T>* Out, const int* active) {
   cq.x = T2;
   cq.z = nullptr;
   cq.out = T3;
+  c->add_bytes(PINT_PROF_COMBO, combo_bytes(*this, cq, active));
   { PROF(c, PINT_PROF_COMBO, 1); launch_combo<T>(cq, st); }
   // swap + (tau K_p)^{-1}: Out[p] = MG(T3[mu]), Out[mu] = MG(T3[p])
   mg(1, false, c->j_Kp2s, 2 * J, Out, T3, active, 1);
@@ -457,6 +495,9 @@ void Engine<T>::inner_solve(const cpx<T>* S, cpx<T>* X, int* its_host) {
   const int m = G.m;
   const long long hs = (long long)(m + 1) * m * 2;  // H stride per frequency (doubles)
   const size_t vs = (size_t)J * nb;                 // one basis vector (all frequencies)
+  const double vbytes = (double)nb * 2 * sizeof(T);  // one frequency's vector
+  double its_sum = 0;                                // sum over frequencies of the steps taken
+  c->add_bytes(PINT_PROF_INNER, 3.0 * J * vbytes);
   {
     PROF(c, PINT_PROF_INNER, 4);
     launch_bdot<T>(J, nb, S, S, nb, nb, G.partial, G.g, (long long)(m + 1) * 2, nullptr, false, st);
@@ -474,6 +515,9 @@ void Engine<T>::inner_solve(const cpx<T>* S, cpx<T>* X, int* its_host) {
     // classical Gram-Schmidt with one reorthogonalisation (CGS2) against
     // V_0..V_i for all active frequencies, then the norm of the result
     const int cnt = i + 1;
+    const double act = J * afrac(G.active);
+    its_sum += act;
+    c->add_bytes(PINT_PROF_INNER, (4.0 * cnt + 8.0) * act * vbytes);
     const int nk = 2 * ((cnt + 7) / 8 + 1) + 2 * 1 + 1 + 1 + 1 + 1;
     PROF(c, PINT_PROF_INNER, nk + 1);
     launch_bmdot<T>(J, nb, V, (long long)vs, cnt, Vn, G.cpart, G.H, hs, m, i, false, G.active, st);
@@ -491,6 +535,7 @@ void Engine<T>::inner_solve(const cpx<T>* S, cpx<T>* X, int* its_host) {
     if (*c->h_count == 0) break;
   }
   active_freqs = 0;
+  c->add_bytes(PINT_PROF_INNER, (its_sum + J) * vbytes);
   {
     PROF(c, PINT_PROF_INNER, 2);
     launch_gmres_finish<T>(G, nb, Z, (long long)vs, X, st);
@@ -504,6 +549,7 @@ void Engine<T>::inner_solve(const cpx<T>* S, cpx<T>* X, int* its_host) {
 template <class T>
 void Engine<T>::freq_solve(cpx<T>* Rin, cpx<T>* Out, int* its_host) {
   if (!c->oseen) {
+    c->add_bytes(PINT_PROF_COMBO, 2 * 2.0 * c->J * c->s.nblk * 2 * sizeof(T));
     {
       PROF(c, PINT_PROF_COMBO, 1);
       launch_stokes_transform<T>(0, c->J, c->s, c->d_tc, Rin, c->st);
@@ -521,13 +567,21 @@ void Engine<T>::freq_solve(cpx<T>* Rin, cpx<T>* Out, int* its_host) {
 // Time DFT of a [K][nblk] FP64 vector into the Hermitian half [J][nblk] and
 // back (Sec. 3.1): tensor cores for the FP32 preconditioner when enabled,
 // else the CUDA-core kernels.
+// algorithmic bytes of one time DFT: the FP64 time slices once, the
+// Hermitian half of the spectrum once in the preconditioner's precision
+template <class T>
+double dft_bytes(const pint_ctx* c) {
+  return 8.0 * c->K * c->s.nblk + (double)c->J * c->s.nblk * 2 * sizeof(T);
+}
 template <class T>
 void dft_forward_any(pint_ctx* c, Engine<T>& e, const double* x, cpx<T>* X) {
+  c->add_bytes(PINT_PROF_DFT_FWD, dft_bytes<T>(c));
   PROF(c, PINT_PROF_DFT_FWD, 1);
   launch_dft_forward<T>(c->K, c->J, c->s.nblk, x, X, e.cosk, e.sink, c->st);
 }
 template <>
 void dft_forward_any<float>(pint_ctx* c, Engine<float>& e, const double* x, cpx<float>* X) {
+  c->add_bytes(PINT_PROF_DFT_FWD, dft_bytes<float>(c));
   PROF(c, PINT_PROF_DFT_FWD, 1);
   if (c->tc.scheme)
     launch_dft_tc_forward(c->tc, c->s.nblk, x, X, c->st);
@@ -536,11 +590,13 @@ void dft_forward_any<float>(pint_ctx* c, Engine<float>& e, const double* x, cpx<
 }
 template <class T>
 void dft_inverse_any(pint_ctx* c, Engine<T>& e, const cpx<T>* X, double* y) {
+  c->add_bytes(PINT_PROF_DFT_INV, dft_bytes<T>(c));
   PROF(c, PINT_PROF_DFT_INV, 1);
   launch_dft_inverse<T>(c->K, c->J, c->s.nblk, X, y, e.cosk, e.sink, c->st);
 }
 template <>
 void dft_inverse_any<float>(pint_ctx* c, Engine<float>& e, const cpx<float>* X, double* y) {
+  c->add_bytes(PINT_PROF_DFT_INV, dft_bytes<float>(c));
   PROF(c, PINT_PROF_DFT_INV, 1);
   if (c->tc.scheme)
     launch_dft_tc_inverse(c->tc, c->s.nblk, X, y, c->st);
@@ -587,6 +643,8 @@ bool valid_params(const pint_params* p, std::string& why) {
     return why = "multigrid / Chebyshev / Uzawa counts must be positive", false;
   if (!(p->uzawa_mu > 0) || !(p->sor_omega > 0) || !(p->sor_omega < 2))
     return why = "uzawa_mu must be positive and sor_omega in (0, 2)", false;
+  if (!(p->sor_omega_conv >= 0) || !(p->sor_omega_conv < 2))
+    return why = "sor_omega_conv must be 0 (same as sor_omega) or in (0, 2)", false;
   return true;
 }
 
@@ -701,6 +759,7 @@ pint_status build(pint_ctx* c) {
   c->conv = p.wind != PINT_WIND_NONE;
   c->gwind = p.wind == PINT_WIND_TWO_VORTEX || p.wind == PINT_WIND_NODAL;
   c->fp32 = p.prec == PINT_PREC_FP32;
+  c->omega_conv = p.sor_omega_conv > 0 ? p.sor_omega_conv : p.sor_omega;
   c->m_in = p.fixed_inner_its > 0 ? p.fixed_inner_its : p.inner_maxit;
   const int N = c->N, J = c->J;
   Slots& s = c->s;
@@ -1001,11 +1060,13 @@ void kkt(pint_ctx* c, const double* x, double* y) {
   a.nst = c->gwind ? c->nst64[0] : nullptr;
   a.x = x;
   a.y = y;
+  c->add_bytes(PINT_PROF_KKT_MV, 16.0 * c->K * c->s.nblk);
   PROF(c, PINT_PROF_KKT_MV, 2);
   launch_kkt_matvec(a, c->st);
 }
 
 void apply_prec(pint_ctx* c, const double* r, double* z, int* its) {
+  PROF(c, PINT_PROF_APPLY, 0);
   if (c->fp32)
     c->e32.apply(r, z, its);
   else
@@ -1015,6 +1076,7 @@ void apply_prec(pint_ctx* c, const double* r, double* z, int* its) {
 inline int mdot_kernels(int cnt) { return 2 * ((cnt + 7) / 8); }
 
 double dot_dev(pint_ctx* c, const double* a, const double* b, long long n) {
+  c->add_bytes(PINT_PROF_OUTER, (a == b ? 8.0 : 16.0) * n);
   {
     PROF(c, PINT_PROF_OUTER, mdot_kernels(1));
     launch_mdot(a, 1, b, n, c->opart, c->oh, c->st);
@@ -1046,6 +1108,7 @@ pint_status fgmres(pint_ctx* c, double* x, pint_solve_info* info) {
   }
   // r = b - A x
   kkt(c, x, c->ot);
+  c->add_bytes(PINT_PROF_OUTER, 24.0 * n);
   {
     PROF(c, PINT_PROF_OUTER, 1);
     launch_axpby(1.0, c->ob, -1.0, c->ot, n, st);
@@ -1055,6 +1118,7 @@ pint_status fgmres(pint_ctx* c, double* x, pint_solve_info* info) {
   int total = 0;
   std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), y(m);
   while (total < c->p.outer_maxit && relres > c->p.outer_tol) {
+    c->add_bytes(PINT_PROF_OUTER, 16.0 * n);
     {
       PROF(c, PINT_PROF_OUTER, 1);
       launch_axpby(1.0 / beta, c->ot, 0.0, c->oV, n, st);
@@ -1079,6 +1143,7 @@ pint_status fgmres(pint_ctx* c, double* x, pint_solve_info* info) {
       cudaStreamSynchronize(st);
       auto a2 = now();
       // CGS2
+      c->add_bytes(PINT_PROF_OUTER, (4.0 * i + 11.0) * 8.0 * n);
       {
         PROF(c, PINT_PROF_OUTER, 2 * mdot_kernels(i + 1) + 2 + mdot_kernels(1));
       launch_mdot(c->oV, i + 1, Vn, n, c->opart, c->oh, st);
@@ -1102,6 +1167,7 @@ pint_status fgmres(pint_ctx* c, double* x, pint_solve_info* info) {
       for (int l = 0; l <= i; ++l) H[(size_t)l * m + i] = c->h_pinned[l] + c->h_pinned[i + 1 + l];
       H[(size_t)(i + 1) * m + i] = hn;
       if (hn != 0.0) {
+        c->add_bytes(PINT_PROF_OUTER, 16.0 * n);
         PROF(c, PINT_PROF_OUTER, 1);
         launch_axpby(1.0 / hn, Vn, 0.0, Vn, n, st);
       }
@@ -1133,11 +1199,13 @@ pint_status fgmres(pint_ctx* c, double* x, pint_solve_info* info) {
     }
     for (int l = 0; l < k; ++l) c->h_pinned[l] = -y[l];
     cudaMemcpyAsync(c->oh, c->h_pinned, sizeof(double) * k, cudaMemcpyHostToDevice, st);
+    c->add_bytes(PINT_PROF_OUTER, (k + 2.0) * 8.0 * n);
     {
       PROF(c, PINT_PROF_OUTER, 1);
       launch_maxpy(c->oZ, k, c->oh, x, n, st);  // x += Z y
     }
     kkt(c, x, c->ot);
+    c->add_bytes(PINT_PROF_OUTER, 24.0 * n);
     {
       PROF(c, PINT_PROF_OUTER, 1);
       launch_axpby(1.0, c->ob, -1.0, c->ot, n, st);
@@ -1192,6 +1260,7 @@ void pint_default_params(pint_params* p) {
   p->fixed_inner_its = 0;
   p->linear = 0;
   p->dft_mode = PINT_DFT_AUTO;
+  p->sor_omega_conv = 0.0;
 }
 
 size_t pint_estimate_device_bytes(const pint_params* p) {
@@ -1683,6 +1752,7 @@ pint_status pint_profile_enable(pint_handle h, unsigned mask) {
   for (int i = 0; i < PINT_PROF_CLASSES; ++i) {
     h->prof_launch[i] = h->prof_timed[i] = 0;
     h->prof_ms[i] = 0.0;
+    h->prof_bytes[i] = 0.0;
   }
   return PINT_OK;
 }
@@ -1695,6 +1765,7 @@ pint_status pint_profile_read(pint_handle h, pint_profile* out) {
     out->launches[i] = h->prof_launch[i];
     out->timed[i] = h->prof_timed[i];
     out->ms[i] = h->prof_ms[i];
+    out->bytes[i] = h->prof_bytes[i];
   }
   return PINT_OK;
 }
@@ -1822,9 +1893,10 @@ pint_status mg_noalloc_T(pint_ctx* c, Engine<T>& e, int which, int j, const doub
   L.cycles = c->p.mg_cycles;
   L.pre = c->p.mg_pre;
   L.post = c->p.mg_post;
-  L.omega = c->p.sor_omega;
+  L.omega = c->oseen && space == 2 ? c->omega_conv : c->p.sor_omega;
   L.space = space;
   L.conv = (which == 1 || which == 2) ? c->conv : false;
+  L.no_tune = true;  // the tuner's bookkeeping allocates on the first launch of a shape
   launch_mg<T>(L, c->st);
   noalloc_stage_out<T><<<(n * n + 255) / 256, 256, 0, c->st>>>(xfield, out, n * n);
   return c->launched("pint_mg_apply_noalloc") ? PINT_OK : PINT_ERR_CUDA;

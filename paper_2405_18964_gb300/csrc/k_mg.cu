@@ -536,10 +536,20 @@ __device__ void sor_colour_b(int n, const BLay& b, cpx<T>* X, const cpx<T>* B, c
   }
 }
 
+// Class-blocked size (complex elements) of the Q2 level with n nodes per side.
+__host__ __device__ __forceinline__ long long q2b_level_size(int n) {
+  const long long w6 = (n + 5) / 6;
+  return 36 * w6 * w6;
+}
+
 template <class T, bool CONV, bool CW>
 __global__ void __launch_bounds__(1024, 1) mg_q2b_kernel(MGLaunch<T> L) {
   __shared__ cpx<T> sw[100];
   __shared__ cpx<T> sdi[9];
+  // iterates of the levels in L.smem_levels live in dynamic shared memory for
+  // the whole solve (each colour phase then reads its neighbours on chip);
+  // right-hand sides, residuals and the other levels stay in the workspace
+  extern __shared__ __align__(16) unsigned char mg_dsm[];
   const FieldJob jb = L.jobs[blockIdx.x];
   if (L.active && !L.active[jb.freq]) return;
   const OpCoef oc = L.ops[jb.op];
@@ -551,7 +561,19 @@ __global__ void __launch_bounds__(1024, 1) mg_q2b_kernel(MGLaunch<T> L) {
   const int last = nl - 1;
   const double* inv = L.coarse_inv + (size_t)jb.op * PINT_NC_MAX * PINT_NC_MAX * 2;
   cpx<T>* ws = L.ws + (size_t)blockIdx.x * L.fields_per_job * L.lay.per_job;
-  auto Xl = [&](int l) { return ws + L.lay.off_x[l]; };
+  cpx<T>* xlev[PINT_MAXLEV];
+  {
+    long long so = 0;
+    for (int l = 0; l < nl; ++l) {
+      if ((L.smem_levels >> l) & 1u) {
+        xlev[l] = reinterpret_cast<cpx<T>*>(mg_dsm) + so;
+        so += q2b_level_size(L.lay.n[l]);
+      } else {
+        xlev[l] = ws + L.lay.off_x[l];
+      }
+    }
+  }
+  auto Xl = [&](int l) { return xlev[l]; };
   auto Bl = [&](int l) { return ws + L.lay.off_b[l]; };
   auto Rl = [&](int l) { return ws + L.lay.off_r[l]; };
   const int n0 = L.lay.n[0];
@@ -736,25 +758,77 @@ int cta_threads(int njobs) {
 }
 
 // ---------------------------------------------------------------------------
-// Autotuner of the multigrid CTA size.  For each launch shape (space, finest
-// nodes per side, job count, precision, operator variant) six launches
-// after a short warm-up try 256, 512 and 1024 threads per CTA twice each
-// (interleaved), timed by CUDA events on the launch stream, and every later
-// launch of that shape uses the fastest on average.  The choice
-// does not change the results: every node's update is the same arithmetic
-// whichever thread performs it, and the nodes of a colour are independent.
+// Shared-memory staging of the Q2 multigrid iterates.  Levels are taken
+// finest first while their class-blocked iterates fit in what a CTA may hold
+// beside the kernel's static arrays (a level that does not fit is skipped
+// and coarser ones are still tried).  Staging changes where the iterate
+// lives, not the arithmetic: results are identical either way.
+// ---------------------------------------------------------------------------
+template <class T>
+size_t q2_smem_budget() {
+  static const size_t budget = [] {
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    size_t stat = 0;
+    cudaFuncAttributes fa{};
+    if (cudaFuncGetAttributes(&fa, mg_q2b_kernel<T, true, true>) == cudaSuccess) stat = fa.sharedSizeBytes;
+    cudaGetLastError();
+    const size_t b = optin > (int)stat + 1024 ? (size_t)optin - stat - 1024 : 0;
+    // allow every instantiation to use up to the budget (once per process)
+    cudaFuncSetAttribute(mg_q2b_kernel<T, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b);
+    cudaFuncSetAttribute(mg_q2b_kernel<T, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b);
+    cudaFuncSetAttribute(mg_q2b_kernel<T, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b);
+    cudaGetLastError();
+    return b;
+  }();
+  return budget;
+}
+
+template <class T>
+unsigned q2_smem_plan(const MGLayout& lay, size_t budget, size_t* bytes) {
+  unsigned mask = 0;
+  size_t tot = 0;
+  for (int l = 0; l < lay.nlev; ++l) {
+    const size_t sz = (size_t)q2b_level_size(lay.n[l]) * sizeof(cpx<T>);
+    if (tot + sz <= budget) {
+      mask |= 1u << l;
+      tot += sz;
+    }
+  }
+  *bytes = tot;
+  return mask;
+}
+
+// ---------------------------------------------------------------------------
+// Autotuner of the multigrid launches.  For each launch shape (space, finest
+// nodes per side, job count, precision, operator variant) the launches
+// after a short warm-up try every candidate -- 256, 512 and 1024 threads per
+// CTA, and for velocity fields each with and without the shared-memory
+// staging of the iterates -- twice each (interleaved), timed by CUDA events
+// on the launch stream; every later launch of that shape uses the fastest
+// on average.  The choice does not change the results: every node's update
+// is the same arithmetic whichever thread performs it and wherever the
+// iterate is held, and the nodes of a colour are independent.
 // ---------------------------------------------------------------------------
 namespace {
-constexpr int TUNE_CAND[3] = {256, 512, 1024};
+struct TuneCand {
+  int threads;
+  bool smem;
+};
+constexpr TuneCand TUNE_CAND[6] = {{256, false}, {512, false}, {1024, false},
+                                   {256, true},  {512, true},  {1024, true}};
+constexpr int TUNE_MAXC = 6;
 constexpr int TUNE_WARMUP = 3;  // launches of a shape before timing (module loading, first touch)
 constexpr int TUNE_REPS = 2;    // timed launches per candidate (interleaved)
-constexpr int TUNE_SLOTS = 3 * TUNE_REPS;
+constexpr int TUNE_MAXSLOTS = TUNE_MAXC * TUNE_REPS;
 struct MgTune {
+  int ncand = 3;  // candidates of this shape: the first ncand of TUNE_CAND
   int seen = 0;
   int best = -1;  // index into TUNE_CAND once decided
-  int next = 0;   // next timing slot; slot i times candidate i % 3
-  float ms[TUNE_SLOTS];
-  cudaEvent_t a[TUNE_SLOTS] = {}, b[TUNE_SLOTS] = {};
+  int next = 0;   // next timing slot; slot i times candidate i % ncand
+  float ms[TUNE_MAXSLOTS];
+  cudaEvent_t a[TUNE_MAXSLOTS] = {}, b[TUNE_MAXSLOTS] = {};
   MgTune() {
     for (float& v : ms) v = -1.f;
   }
@@ -764,19 +838,22 @@ std::mutex g_tune_mu;
 std::map<MgKey, MgTune> g_tune;
 std::atomic<bool> g_tune_on{true};
 
-// Threads for this launch; slot >= 0 means "time this launch into slot".
-int tune_pick(const MgKey& key, int fallback, int& slot, cudaEvent_t& ea, cudaEvent_t& eb) {
+// Candidate for this launch; slot >= 0 means "time this launch into slot".
+// ncand: 3 (CTA sizes only) or 6 (also the shared-memory staging).
+TuneCand tune_pick(const MgKey& key, int ncand, TuneCand fallback, int& slot, cudaEvent_t& ea, cudaEvent_t& eb) {
   slot = -1;
   if (!g_tune_on.load()) return fallback;
   std::lock_guard<std::mutex> lk(g_tune_mu);
   MgTune& t = g_tune[key];
+  t.ncand = ncand;
+  const int nslots = t.ncand * TUNE_REPS;
   if (t.seen < TUNE_WARMUP) {
     ++t.seen;
     return fallback;
   }
   if (t.best < 0) {
     bool all = true;
-    for (int i = 0; i < TUNE_SLOTS; ++i) {
+    for (int i = 0; i < nslots; ++i) {
       if (t.ms[i] < 0.f && i < t.next) {
         const cudaError_t q = cudaEventQuery(t.b[i]);
         if (q == cudaSuccess)
@@ -787,23 +864,23 @@ int tune_pick(const MgKey& key, int fallback, int& slot, cudaEvent_t& ea, cudaEv
       all = all && t.ms[i] >= 0.f;
     }
     if (all) {
-      float sum[3] = {0.f, 0.f, 0.f};
-      for (int i = 0; i < TUNE_SLOTS; ++i) sum[i % 3] += t.ms[i];
+      float sum[TUNE_MAXC] = {};
+      for (int i = 0; i < nslots; ++i) sum[i % t.ncand] += t.ms[i];
       t.best = 0;
-      for (int i = 1; i < 3; ++i)
+      for (int i = 1; i < t.ncand; ++i)
         if (sum[i] < sum[t.best]) t.best = i;
-      for (int i = 0; i < 3; ++i) t.ms[i] = sum[i] / TUNE_REPS;  // reported: mean per candidate
-      for (int i = 0; i < TUNE_SLOTS; ++i) {
+      for (int i = 0; i < t.ncand; ++i) t.ms[i] = sum[i] / TUNE_REPS;  // reported: mean per candidate
+      for (int i = 0; i < nslots; ++i) {
         cudaEventDestroy(t.a[i]);
         cudaEventDestroy(t.b[i]);
       }
-    } else if (t.next < TUNE_SLOTS) {
+    } else if (t.next < nslots) {
       slot = t.next++;
       cudaEventCreate(&t.a[slot]);
       cudaEventCreate(&t.b[slot]);
       ea = t.a[slot];
       eb = t.b[slot];
-      return TUNE_CAND[slot % 3];
+      return TUNE_CAND[slot % t.ncand];
     } else {
       return fallback;  // a timing is still in flight
     }
@@ -817,40 +894,57 @@ void mg_autotune_enable(bool on) { g_tune_on.store(on); }
 std::string mg_autotune_report() {
   std::lock_guard<std::mutex> lk(g_tune_mu);
   std::string out;
-  char line[256];
+  char line[512];
   for (const auto& kv : g_tune) {
     const auto& k = kv.first;
     const MgTune& t = kv.second;
-    snprintf(line, sizeof line, "space=%d n=%d jobs=%d %s variant=%d: 256:%.3f 512:%.3f 1024:%.3f ms -> %d\n",
-             std::get<0>(k), std::get<1>(k), std::get<2>(k), std::get<3>(k) == 4 ? "fp32" : "fp64",
-             std::get<4>(k), t.ms[0], t.ms[1], t.ms[2], t.best >= 0 ? TUNE_CAND[t.best] : 0);
+    int n = snprintf(line, sizeof line, "space=%d n=%d jobs=%d %s variant=%d:", std::get<0>(k), std::get<1>(k),
+                     std::get<2>(k), std::get<3>(k) == 4 ? "fp32" : "fp64", std::get<4>(k));
+    for (int i = 0; i < t.ncand && n < (int)sizeof line; ++i)
+      n += snprintf(line + n, sizeof line - n, " %d%s:%.3f", TUNE_CAND[i].threads, TUNE_CAND[i].smem ? "s" : "",
+                    t.best >= 0 ? t.ms[i] : -1.f);
+    if (n < (int)sizeof line)
+      snprintf(line + n, sizeof line - n, " ms -> %d%s\n", t.best >= 0 ? TUNE_CAND[t.best].threads : 0,
+               t.best >= 0 && TUNE_CAND[t.best].smem ? "s" : "");
     out += line;
   }
   return out;
 }
 
 template <class T>
-void launch_mg(const MGLaunch<T>& L, cudaStream_t st) {
-  if (L.njobs <= 0) return;
+void launch_mg(const MGLaunch<T>& Lin, cudaStream_t st) {
+  if (Lin.njobs <= 0) return;
+  MGLaunch<T> L = Lin;
   const int variant = L.conv ? 2 : (L.cw ? 1 : 0);
   int slot = -1;
   cudaEvent_t ea = nullptr, eb = nullptr;
+  // shared-memory staging plan of the velocity iterates (nothing for Q1)
+  size_t sbytes = 0;
+  const unsigned plan = L.space == 2 ? q2_smem_plan<T>(L.lay, q2_smem_budget<T>(), &sbytes) : 0u;
+  const bool can_stage = plan != 0;
   // When only some frequencies are still active (late inner iterations), the
-  // few live fields get larger CTAs; otherwise the tuned size for this shape.
+  // few live fields get larger CTAs; otherwise the tuned choice for this shape.
   const bool tail = L.active_jobs > 0 && L.active_jobs < L.njobs;
-  const int threads = tail ? cta_threads(L.active_jobs)
-                           : tune_pick(MgKey(L.space, L.lay.n[0], L.njobs, (int)sizeof(T), variant),
-                                       cta_threads(L.njobs), slot, ea, eb);
-  dim3 grid(L.njobs), block(threads);
+  TuneCand pick;
+  if (L.no_tune)
+    pick = TuneCand{cta_threads(L.njobs), can_stage};
+  else if (tail)
+    pick = TuneCand{cta_threads(L.active_jobs), can_stage};
+  else
+    pick = tune_pick(MgKey(L.space, L.lay.n[0], L.njobs, (int)sizeof(T), variant), can_stage ? 6 : 3,
+                     TuneCand{cta_threads(L.njobs), can_stage}, slot, ea, eb);
+  L.smem_levels = pick.smem ? plan : 0u;
+  const size_t dyn = pick.smem ? sbytes : 0;
+  dim3 grid(L.njobs), block(pick.threads);
   if (slot >= 0) cudaEventRecord(ea, st);
   if (L.space == 2) {
     // one velocity field per CTA, class-blocked layout in the workspace
     if (L.conv)
-      mg_q2b_kernel<T, true, true><<<grid, block, 0, st>>>(L);
+      mg_q2b_kernel<T, true, true><<<grid, block, dyn, st>>>(L);
     else if (L.cw)
-      mg_q2b_kernel<T, false, true><<<grid, block, 0, st>>>(L);
+      mg_q2b_kernel<T, false, true><<<grid, block, dyn, st>>>(L);
     else
-      mg_q2b_kernel<T, false, false><<<grid, block, 0, st>>>(L);
+      mg_q2b_kernel<T, false, false><<<grid, block, dyn, st>>>(L);
   } else {
     mg_kernel<T, 1, false, false><<<grid, block, 0, st>>>(L);
   }

@@ -53,6 +53,8 @@ struct MGLaunch {
   int space;  // 2 = Q2 (velocity component), 1 = Q1 (pressure)
   bool conv;
   int active_jobs;  // > 0: jobs whose frequency is still active (sizes the CTAs), 0: all
+  bool no_tune;     // true: fixed CTA size, the autotuner is not consulted (it would allocate on first use)
+  unsigned smem_levels;  // Q2 multigrid: bit l set = level l's iterate in shared memory (set by launch_mg)
 };
 
 #define PINT_NC_MAX 9

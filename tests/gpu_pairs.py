@@ -45,6 +45,7 @@ def make_pair(kind, level, K, beta=1e-2, nu=1e-2, prec=0, T=1.0, **kw):
 def settings_of(G):
     p = G.params
     return inexact.Settings(mg_cycles=p.mg_cycles, mg_pre=p.mg_pre, mg_post=p.mg_post, sor_omega=p.sor_omega,
+                            sor_omega_conv=p.sor_omega_conv if p.sor_omega_conv > 0 else None,
                             cheb_steps=p.cheb_steps, uzawa_steps=p.uzawa_steps, uzawa_mu=p.uzawa_mu,
                             inner_tol=p.inner_tol, inner_maxit=p.inner_maxit)
 

@@ -128,3 +128,42 @@ def test_host_convection_stencils_match_the_oracle(wind):
             assert np.abs(_band_to_dense(st, m, hw) - ref).max() <= 1e-14 * np.abs(ref).max()
     with pytest.raises(binding.PintError):
         binding.convection_stencils(binding.default_params(kind=1, level=level, wind=1, x0=-1.0, x1=1.0))
+
+
+class _FakeCudaTensor:
+    """Stands in for a CUDA tensor in the binding's argument checks (no GPU)."""
+
+    def __init__(self, numel):
+        self._n = numel
+        self.is_cuda = True
+        self.dtype = "torch.complex128"
+
+    def data_ptr(self):
+        return 0
+
+    def is_contiguous(self):
+        return True
+
+    def numel(self):
+        return self._n
+
+
+class _FakeProblem:
+    def __init__(self):
+        self.h = None
+        self.sizes = binding.Sizes(N=8, n_t=4, J=3, n_s=17 * 17, n_q=9 * 9, n_blk=4 * 289 + 2 * 81)
+
+
+@pytest.mark.parametrize("method", ["mg_apply_noalloc", "component_apply"])
+@pytest.mark.parametrize("which,good", [("mg_W", 289), ("mg_Kp", 81)])
+def test_component_field_length_checked_before_any_call(method, which, good):
+    """A field of the wrong length is refused on the host (ValueError) before
+    the library is called: the C entry points take no length and would read
+    or write past the end of the caller's buffer."""
+    fn = getattr(binding.Problem, method)
+    for n in (good - 1, good + 1, 0):
+        with pytest.raises(ValueError):
+            fn(_FakeProblem(), which, 0, _FakeCudaTensor(n), _FakeCudaTensor(good))
+        with pytest.raises(ValueError):
+            fn(_FakeProblem(), which, 0, _FakeCudaTensor(good), _FakeCudaTensor(n))
+    assert binding.component_len(_FakeProblem().sizes, 6) == 4 * 289 + 2 * 81

@@ -7,7 +7,9 @@ offers pint_mg_apply_noalloc, which takes its scratch from one fixed device
 array.  These tests call it through the C ABI and compare it with the
 ordinary entry point (pint_component_apply, same solve, handle workspace) on
 two calls in a row, so the second call runs on the scratch the first one
-left behind.  This file is collected last on purpose.
+left behind, and check that repeated calls allocate nothing (the device's
+free memory does not move, and the multigrid autotuner, whose bookkeeping
+allocates, is never consulted).  This file is collected last on purpose.
 """
 import numpy as np
 import pytest
@@ -40,6 +42,29 @@ def test_noalloc_matches_component_apply(kind, level, K, prec, which):
         G.mg_apply_noalloc(which, j, x, got)
         torch.cuda.synchronize()
         assert relerr(got.cpu().numpy(), ref.cpu().numpy()) <= tol, (call, j)
+    G.close()
+
+
+def test_noalloc_repeated_calls_allocate_nothing():
+    """Twelve calls with the autotuner switched on (more than the tuner's
+    three warm-up and six timed launches of a shape): the free device memory
+    is the same after the last call as after the first, the tuner has no
+    entry for a single-field launch, and the result stays the same."""
+    binding.autotune(True)
+    P, G = make_pair("stokes", 5, 4, prec=1, inner_maxit=4)
+    n = P.grid.ns
+    x = to_dev(inputs.random_vector(n, 7, np.complex128), "complex128")
+    y = torch.zeros(n, dtype=torch.complex128, device="cuda")
+    first = torch.zeros_like(y)
+    G.mg_apply_noalloc("mg_W", 1, x, first)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(12):
+        G.mg_apply_noalloc("mg_W", 1, x, y)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    assert torch.equal(y, first)
+    assert not [ln for ln in binding.autotune_report().splitlines() if " jobs=1 " in ln]
     G.close()
 
 
