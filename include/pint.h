@@ -392,10 +392,22 @@ const char* pint_server_last_error(void);
  * variant) six launches after the first three (untimed: module loading,
  * first touch of the workspaces) run with 256, 512 and 1024 threads per
  * CTA, twice each, timed by CUDA events on the launch stream; later
- * launches use the fastest on average.  Results do not depend on the choice.  pint_autotune(0) restores
- * the fixed heuristic (1024 threads up to one field per SM, 512 up to two,
- * else 256). */
+ * launches use the fastest on average.  For velocity fields the candidates
+ * also include the shared-memory staging of the multigrid iterates (every
+ * level whose iterate fits, finest first).  Results do not depend on the
+ * choice.  pint_autotune(0) restores the fixed heuristic (1024 threads up to
+ * one field per SM, 512 up to two, else 256; staging whenever it fits), or
+ * the choice of pint_mg_launch_config. */
 void pint_autotune(int on);
+/* The multigrid launch choice used while the tuner is off (pint_autotune(0)),
+ * process-wide: threads per CTA (256, 512, 1024; 0 = the fixed heuristic)
+ * and the kernel variant for velocity fields: 1 or -1 = the fastest that
+ * applies (the kernel with compile-time level sizes for the Stokes W_j on
+ * grids of 4..256 elements per side, else the general kernel with the
+ * iterates staged in shared memory where they fit), 0 = the general kernel
+ * without staging.  Results agree to rounding; PINT_ERR_ARG for other
+ * values. */
+pint_status pint_mg_launch_config(int threads, int staging);
 /* The tuner's decisions as text, one launch shape per line, written to buf
  * (NUL-terminated, truncated to len); returns the size needed. */
 size_t pint_autotune_report(char* buf, size_t len);

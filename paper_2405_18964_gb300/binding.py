@@ -92,6 +92,7 @@ _SIGS = {
     "pint_freq_block_solve": (ctypes.c_int, [_P, _P, _P, _P]),
     "pint_component_apply": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P, _P]),
     "pint_mg_apply_noalloc": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P, _P]),
+    "pint_mg_launch_config": (ctypes.c_int, [ctypes.c_int, ctypes.c_int]),
     "pint_profile_enable": (ctypes.c_int, [_P, ctypes.c_uint]),
     "pint_profile_read": (ctypes.c_int, [_P, ctypes.POINTER(Profile)]),
     "pint_debug_inject": (ctypes.c_int, [_P, ctypes.c_int]),
@@ -342,6 +343,11 @@ def convection_stencils(params, level_index=0, wind=None):
 def autotune(on=True):
     """Switch the multigrid CTA-size autotuner on or off (process-wide)."""
     lib().pint_autotune(1 if on else 0)
+
+
+def mg_launch_config(threads=0, staging=-1):
+    """Multigrid launch choice while the tuner is off (see pint.h)."""
+    _check(lib().pint_mg_launch_config(int(threads), int(staging)), None)
 
 
 def autotune_report():

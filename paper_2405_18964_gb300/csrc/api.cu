@@ -711,8 +711,10 @@ MGLayout make_layout(int nlev, int N, int space) {
   // nodes), so level 0 is copied too
   auto lsize = [&](int l) -> long long {
     if (space == 2) {
-      const long long w6 = (L.n[l] + 5) / 6;
-      return 36 * w6 * w6;
+      // class-blocked layout, or the padded per-type layout of the
+      // compile-time-sized kernel, whichever is larger
+      const long long w6 = (L.n[l] + 5) / 6, Nl = N >> l;
+      return std::max(36 * w6 * w6, 4 * (Nl + 1) * (long long)q2p_pitch((int)Nl));
     }
     return (long long)L.n[l] * L.n[l];
   };
@@ -1725,6 +1727,19 @@ pint_status pint_component_apply(pint_handle h, int which, int j, const double* 
 }
 
 void pint_autotune(int on) { mg_autotune_enable(on != 0); }
+
+pint_status pint_mg_launch_config(int threads, int staging) {
+  if (threads != 0 && threads != 256 && threads != 512 && threads != 1024) {
+    g_err = "threads must be 0, 256, 512 or 1024";
+    return PINT_ERR_ARG;
+  }
+  if (staging < -1 || staging > 1) {
+    g_err = "staging must be -1, 0 or 1";
+    return PINT_ERR_ARG;
+  }
+  mg_fixed_config(threads, staging);
+  return PINT_OK;
+}
 
 size_t pint_autotune_report(char* buf, size_t len) {
   const std::string r = mg_autotune_report();

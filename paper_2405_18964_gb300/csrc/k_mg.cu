@@ -25,63 +25,12 @@
 #include <tuple>
 
 #include "kernels.h"
+#include "mg_weights.cuh"
 
 namespace pint {
 
 constexpr int MG_THREADS = 256;
 
-
-// ----------------------------------------------------------------------------
-// Stencil weights.  On the uniform grid the 2-D weights of a constant-
-// coefficient operator a M + b K depend only on the node type: for Q2 the
-// parities of (ix, iy) (vertex / midpoint), for Q1 whether ix, iy lie on the
-// boundary (natural conditions give half rows there).  They are formed in
-// FP64 from the 1-D bands and rounded once to T; the convection part (which
-// varies per node) comes from a per-node table built the same way.
-// ----------------------------------------------------------------------------
-template <int SP>
-__device__ __forceinline__ int ntypes() { return SP == 2 ? 4 : 9; }
-template <int SP>
-__device__ __forceinline__ int nstencil() { return SP == 2 ? 25 : 9; }
-
-// representative node index along one axis for a node type coordinate
-template <int SP>
-__device__ __forceinline__ int type_rep(int t, int n) {
-  if (SP == 2) return t ? 1 : 2;           // midpoint : vertex
-  return t == 0 ? 0 : (t == 1 ? 1 : n - 1);  // left boundary : interior : right boundary
-}
-template <int SP>
-__device__ __forceinline__ int node_type(int ix, int iy, int n) {
-  if (SP == 2) return (ix & 1) + 2 * (iy & 1);
-  const int tx = ix == 0 ? 0 : (ix == n - 1 ? 2 : 1);
-  const int ty = iy == 0 ? 0 : (iy == n - 1 ? 2 : 1);
-  return tx + 3 * ty;
-}
-
-// sw[type][k] = a M + b K at level l (FP64 -> T), sdi[type] = 1 / diagonal.
-template <class T, int SP>
-__device__ void level_weights(const Tabs<double>& t64, int l, int n, cpx<double> a, double b, cpx<T>* sw,
-                              cpx<T>* sdi) {
-  constexpr int W = SP == 2 ? 5 : 3;
-  const double* tab = SP == 2 ? t64.q2[l] : t64.q1[l];
-  const int nt = ntypes<SP>(), ns = nstencil<SP>();
-  for (int q = threadIdx.x; q < nt * ns; q += blockDim.x) {
-    const int type = q / ns, k = q % ns;
-    const int dx = k % W, dy = k / W;
-    const int tx = SP == 2 ? (type & 1) : type % 3;
-    const int ty = SP == 2 ? (type >> 1) : type / 3;
-    const int ix = type_rep<SP>(tx, n), iy = type_rep<SP>(ty, n);
-    const double mx = tab[(size_t)(0 * n + ix) * W + dx], my = tab[(size_t)(0 * n + iy) * W + dy];
-    const double kx = tab[(size_t)(1 * n + ix) * W + dx], ky = tab[(size_t)(1 * n + iy) * W + dy];
-    const double m2 = mx * my, k2 = kx * my + mx * ky;
-    const cpx<double> w = mkc<double>(a.x * m2 + b * k2, a.y * m2);
-    sw[q] = mkc<T>(T(w.x), T(w.y));
-    if (k == ns / 2) {
-      const double den = w.x * w.x + w.y * w.y;
-      sdi[type] = mkc<T>(T(w.x / den), T(-w.y / den));
-    }
-  }
-}
 
 // (A x) at a node: sum_k w_k x_k (+ c sum_k N_k x_k for convection).
 template <class T, int SP, bool CONV, bool CW>
@@ -837,6 +786,9 @@ using MgKey = std::tuple<int, int, int, int, int>;  // space, n0, njobs, sizeof(
 std::mutex g_tune_mu;
 std::map<MgKey, MgTune> g_tune;
 std::atomic<bool> g_tune_on{true};
+// fixed choice used while the tuner is off: CTA threads (0 = by job count)
+// and staging (-1 = stage whenever the plan holds a level, 0 = never, 1 = always)
+std::atomic<int> g_fixed_threads{0}, g_fixed_staging{-1};
 
 // Candidate for this launch; slot >= 0 means "time this launch into slot".
 // ncand: 3 (CTA sizes only) or 6 (also the shared-memory staging).
@@ -890,6 +842,10 @@ TuneCand tune_pick(const MgKey& key, int ncand, TuneCand fallback, int& slot, cu
 }  // namespace
 
 void mg_autotune_enable(bool on) { g_tune_on.store(on); }
+void mg_fixed_config(int threads, int staging) {
+  g_fixed_threads.store(threads);
+  g_fixed_staging.store(staging);
+}
 
 std::string mg_autotune_report() {
   std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -918,26 +874,37 @@ void launch_mg(const MGLaunch<T>& Lin, cudaStream_t st) {
   const int variant = L.conv ? 2 : (L.cw ? 1 : 0);
   int slot = -1;
   cudaEvent_t ea = nullptr, eb = nullptr;
+  // the compile-time-sized kernel covers the real velocity operators W_j
+  // (its own staging plan); the others run the general kernels
+  // (pint_mg_launch_config with staging 0 selects the general kernels)
+  const bool sized = L.space == 2 && !L.conv && !L.cw && (L.lay.n[0] - 1) / 2 >= 4 &&
+                     (L.lay.n[0] - 1) / 2 <= 256 && (g_tune_on.load() || g_fixed_staging.load() != 0);
   // shared-memory staging plan of the velocity iterates (nothing for Q1)
   size_t sbytes = 0;
-  const unsigned plan = L.space == 2 ? q2_smem_plan<T>(L.lay, q2_smem_budget<T>(), &sbytes) : 0u;
+  const unsigned plan = L.space == 2 && !sized ? q2_smem_plan<T>(L.lay, q2_smem_budget<T>(), &sbytes) : 0u;
   const bool can_stage = plan != 0;
   // When only some frequencies are still active (late inner iterations), the
   // few live fields get larger CTAs; otherwise the tuned choice for this shape.
   const bool tail = L.active_jobs > 0 && L.active_jobs < L.njobs;
   TuneCand pick;
-  if (L.no_tune)
+  if (L.no_tune) {
     pick = TuneCand{cta_threads(L.njobs), can_stage};
-  else if (tail)
+  } else if (!g_tune_on.load()) {
+    const int ft = g_fixed_threads.load(), fs = g_fixed_staging.load();
+    pick = TuneCand{ft > 0 ? ft : cta_threads(tail ? L.active_jobs : L.njobs), can_stage && fs != 0};
+  } else if (tail) {
     pick = TuneCand{cta_threads(L.active_jobs), can_stage};
-  else
-    pick = tune_pick(MgKey(L.space, L.lay.n[0], L.njobs, (int)sizeof(T), variant), can_stage ? 6 : 3,
+  } else {
+    pick = tune_pick(MgKey(L.space, L.lay.n[0], L.njobs, (int)sizeof(T), sized ? 3 : variant), can_stage ? 6 : 3,
                      TuneCand{cta_threads(L.njobs), can_stage}, slot, ea, eb);
+  }
   L.smem_levels = pick.smem ? plan : 0u;
   const size_t dyn = pick.smem ? sbytes : 0;
   dim3 grid(L.njobs), block(pick.threads);
   if (slot >= 0) cudaEventRecord(ea, st);
-  if (L.space == 2) {
+  if (sized && launch_mg_q2p<T>(L, pick.threads, st)) {
+    // launched by the compile-time-sized kernel
+  } else if (L.space == 2) {
     // one velocity field per CTA, class-blocked layout in the workspace
     if (L.conv)
       mg_q2b_kernel<T, true, true><<<grid, block, dyn, st>>>(L);

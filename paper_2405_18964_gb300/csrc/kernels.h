@@ -61,8 +61,28 @@ struct MGLaunch {
 
 template <class T>
 void launch_mg(const MGLaunch<T>& L, cudaStream_t st);
+// Row pitch of one node type's iterate sub-grid in the compile-time-sized
+// velocity multigrid (k_mgp.cu), for a level of N elements per side: the
+// smallest P >= N + 1 with P = ceil((N + 1) / 3) (mod 16), so that the nodes
+// of one colour, taken in order, fall into distinct shared-memory banks;
+// N + 1 for the small levels.
+__host__ __device__ constexpr int q2p_pitch(int N) {
+  const int w3 = (N + 3) / 3;
+  if (w3 <= 4) return N + 1;
+  int p = N + 1;
+  while (p % 16 != w3 % 16) ++p;
+  return p;
+}
+
+// The compile-time-sized velocity multigrid (k_mgp.cu) for the launches it
+// covers; false (nothing launched) for the others.
+template <class T>
+bool launch_mg_q2p(const MGLaunch<T>& L, int threads, cudaStream_t st);
 // CTA-size autotuner of launch_mg (on by default) and its decisions as text.
 void mg_autotune_enable(bool on);
+// Fixed launch choice while the tuner is off (threads 0 = by job count;
+// staging -1 = whenever possible, 0 = never, 1 = whenever possible).
+void mg_fixed_config(int threads, int staging);
 std::string mg_autotune_report();
 
 template <class T>
