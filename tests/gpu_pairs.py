@@ -6,6 +6,10 @@ from paper_2405_18964_gb300 import binding
 
 FP64_TOL = 1e-12   # FP64 preconditioner / component parity (relative, max-norm)
 FP32_TOL = 1e-5    # FP32 preconditioner / component parity
+# Where FP32 execution of the method itself (tests/fp32_emulation.py) lands
+# further than FP32_TOL from the FP64 oracle, the GPU's FP32 result is held to
+# this multiple of the emulation's distance instead.
+FP32_EMU_FACTOR = 2.0
 # FP64 bar for pressure values that pass through the multigrid on the
 # corner-pinned pressure Laplacian K_p at 64 x 64: evaluating the same K_p in
 # band form (M1 X K1^T + K1 X M1^T) instead of assembled rows moves the
@@ -124,3 +128,25 @@ def fp32_arnoldi_solves(P, s, freqs, blocks, fixed_its):
         return {j: pc.solve_block(j, blocks[j]) for j in freqs}
     finally:
         inexact.gmres = saved
+
+
+def fp32_emulated_solves(P, s, freqs, blocks, fixed_its):
+    """Frequency-block solves of the oracle's method executed in FP32
+    (tests/fp32_emulation.py), for the bar of FP32 comparisons."""
+    import fp32_emulation
+    em = fp32_emulation.PinT32(P, s, fixed_inner_its=fixed_its)
+    return {j: em.solve_block(j, blocks[j]) for j in freqs}
+
+
+def fp32_emulated_apply(P, s, r, linear=False, fixed_its=0):
+    """The whole preconditioner apply (Algorithm 1/2) with every frequency
+    block solved in FP32 emulation; the time DFT in FP64 with its spectrum
+    rounded to FP32."""
+    import fp32_emulation
+    em = fp32_emulation.PinT32(P, s, fixed_inner_its=fixed_its, linear=linear)
+
+    def block_solver(j, rhs_ylam):
+        g = P.ylam_to_g(rhs_ylam.astype(np.complex64).astype(complex))
+        return P.g_to_ylam(em.solve_block(j, g))
+
+    return P.pc_inverse(r, block_solver)[0]

@@ -11,13 +11,13 @@ final solution, recomputed row by row from the oracle's Kronecker form).
 import numpy as np
 import pytest
 
-from gpu_pairs import (FP32_TOL, FP64_TOL, KP_FP64_TOL, fp32_arnoldi_solves, freq_blocks, make_pair, part_errors,
-                       relerr, settings_of, to_dev)
+from gpu_pairs import (FP32_EMU_FACTOR, FP32_TOL, FP64_TOL, KP_FP64_TOL, fp32_emulated_solves, freq_blocks,
+                       make_pair, part_errors, relerr, settings_of, to_dev)
 
-# FP32 bar at full size: 10x the change of the oracle's own
-# result when only its inner Krylov vectors are rounded to FP32, at least the
-# FP32 apply bar 1e-5.
-FP32_EMULATION_FACTOR = 10.0
+# FP32 bar at full size: 1e-5, or twice the distance from the FP64 oracle of
+# the oracle's own method executed in FP32 (tests/fp32_emulation.py) where
+# that is larger -- at j = K/4 three inner GMRES steps amplify FP32 rounding
+# of the preconditioned vectors beyond 1e-5 (emulated: 1.8e-5).
 from oracle import inexact, layout
 from paper_2405_18964_gb300 import inputs
 
@@ -106,12 +106,14 @@ def test_frequency_block_solves_full_size(prec):
     pc = inexact.PinTPreconditioner(P, settings_of(G), fixed_inner_its=3)
     got = freq_blocks(P, yh.cpu().numpy())
     rs = freq_blocks(P, rh)
-    emu = fp32_arnoldi_solves(P, settings_of(G), SAMPLED_J, rs, 3) if prec else {}
+    emu = fp32_emulated_solves(P, settings_of(G), SAMPLED_J, rs, 3) if prec else {}
     for j in SAMPLED_J:
         ref = pc.solve_block(j, rs[j])
         if prec:
-            bar = max(FP32_TOL, FP32_EMULATION_FACTOR * relerr(emu[j], ref))
-            assert relerr(got[j], ref) <= bar, (j, relerr(got[j], ref), bar)
+            e, e_emu = relerr(got[j], ref), relerr(emu[j], ref)
+            bar = max(FP32_TOL, FP32_EMU_FACTOR * e_emu)
+            print(f"block solve j={j} FP32: GPU {e:.3e}, FP32 emulation {e_emu:.3e}, bar {bar:.3e}")
+            assert e <= bar, (j, e, bar)
         else:
             # pressure through the K_p multigrid: evaluation-order bar (see gpu_pairs)
             e = part_errors(P, got[j], ref)
@@ -216,8 +218,9 @@ def test_preconditioner_apply_full_size(prec):
     err = relerr(got, zo)
     print(f"apply full size prec {prec}: relerr {err:.3e}")
     if prec:
-        emu = relerr(to_time(fp32_arnoldi_solves(P, settings_of(G), freqs, blocks, 3)), zo)
-        assert err <= max(FP32_TOL, FP32_EMULATION_FACTOR * emu), (err, emu)
+        emu = relerr(to_time(fp32_emulated_solves(P, settings_of(G), freqs, blocks, 3)), zo)
+        print(f"apply full size FP32: GPU {err:.3e}, FP32 emulation {emu:.3e}")
+        assert err <= max(FP32_TOL, FP32_EMU_FACTOR * emu), (err, emu)
     else:
         # the pressure values pass through the K_p multigrid (evaluation-order bar, see gpu_pairs)
         s = layout.slots(P)

@@ -10,7 +10,7 @@ solve recomputed row by row.
 import numpy as np
 import pytest
 
-from gpu_pairs import (FP32_TOL, FP64_TOL, KP_FP64_TOL, fp32_arnoldi_solves, freq_blocks, make_pair, part_errors,
+from gpu_pairs import (FP32_TOL, FP64_TOL, KP_FP64_TOL, FP32_EMU_FACTOR, fp32_emulated_solves, freq_blocks, make_pair, part_errors,
                        relerr, settings_of, to_dev)
 from oracle import inexact, layout
 from paper_2405_18964_gb300 import inputs
@@ -69,12 +69,14 @@ def test_oseen_frequency_block_solves_full_size(prec):
     rs = freq_blocks(P, rh)
     sample = [1, J - 1]
     pc = inexact.PinTPreconditioner(P, settings_of(G), fixed_inner_its=2)
-    emu = fp32_arnoldi_solves(P, settings_of(G), sample, rs, 2) if prec else {}
+    emu = fp32_emulated_solves(P, settings_of(G), sample, rs, 2) if prec else {}
     for j in sample:
         ref = pc.solve_block(j, rs[j])
         if prec:
-            bar = max(FP32_TOL, 10.0 * relerr(emu[j], ref))
-            assert relerr(got[j], ref) <= bar, (j, relerr(got[j], ref), bar)
+            e, e_emu = relerr(got[j], ref), relerr(emu[j], ref)
+            bar = max(FP32_TOL, FP32_EMU_FACTOR * e_emu)
+            print(f"Oseen block solve j={j} FP32: GPU {e:.3e}, FP32 emulation {e_emu:.3e}, bar {bar:.3e}")
+            assert e <= bar, (j, e, bar)
         else:
             e = part_errors(P, got[j], ref)
             assert max(e["v"], e["lam"]) <= FP64_TOL and max(e["p"], e["mu"]) <= KP_FP64_TOL, (j, e)
