@@ -37,11 +37,14 @@ WORKLOADS = {
     "stokes64_nt32": dict(kind=0, level=6, K=32, T=1.0, betas=[1e-4], nu=1e-2, x0=0.0, x1=1.0, wind=0),
     # small case the oracle solves in seconds (8x8 grid, n_t = 8)
     "stokes8_nt8": dict(kind=0, level=3, K=8, T=1.0, betas=[1e-2], nu=1e-2, x0=0.0, x1=1.0, wind=0),
-    # Oseen control, 128x128 Q2-Q1 on [-1,1]^2, n_t = 128, nu = 1/100, recirculating wind
-    "oseen128_nt128": dict(kind=1, level=7, K=128, T=1.0, betas=[1e-4], nu=1e-2, x0=-1.0, x1=1.0, wind=1),
+    # Oseen control, 128x128 Q2-Q1 on [-1,1]^2, n_t = 128, nu = 1/100, recirculating wind,
+    # time DFT as a 3xTF32 tensor-core contraction
+    "oseen128_nt128": dict(kind=1, level=7, K=128, T=1.0, betas=[1e-4], nu=1e-2, x0=-1.0, x1=1.0, wind=1,
+                           dft_mode=3, inner_maxit=40),
     # large Oseen control, 256x256, n_t = 128, nu = 1/500, beta = 1e-6, FGMRES(20)
+    # (inner GMRES capped at 40 iterations: the Uzawa-preconditioned blocks need a few)
     "oseen256_nt128": dict(kind=1, level=8, K=128, T=1.0, betas=[1e-6], nu=2e-3, x0=-1.0, x1=1.0, wind=1,
-                           restart=20),
+                           restart=20, inner_maxit=40),
 }
 # FGMRES iterations per solve measured on the GB300 (FP64 and FP32 preconditioner
 # agree) for the middle beta of each workload; used to extrapolate the oracle's
@@ -63,6 +66,8 @@ def parse():
     ap.add_argument("--rate", type=float, default=1.0, help="serve: Poisson arrival rate (requests/s)")
     ap.add_argument("--slots", type=int, default=8, help="serve: worker slots of the server")
     ap.add_argument("--serve-prec", type=int, default=1, choices=[0, 1], help="serve: 1 = FP32 preconditioner")
+    ap.add_argument("--share", type=int, default=1, choices=[0, 1],
+                    help="serve: 1 = batch the frequency solves of the requests on the GPU in shared launches")
     ap.add_argument("--max-level", type=int, default=7, help="serve: largest grid level drawn (7 = 128x128)")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--fp64-budget-s", type=float, default=120.0,
@@ -166,27 +171,33 @@ def peaks_bf16():
     return 1700.0, "fallback (sustained)"
 
 
-def dft_report(sizes, dft, bf16_peak):
-    """Time DFT of the FP32 preconditioner (split-BF16 x6 on tcgen05 for
-    n_t <= 256): algorithmic bytes (FP64 time slices in, complex FP32
-    Hermitian half out, or the reverse) and tensor flops as issued (six
-    128 x npad x 32 MMA products per tile and reduction chunk)."""
+def dft_report(sizes, dft, bf16_peak, mode=0):
+    """Time DFT of the FP32 preconditioner (tcgen05 for n_t <= 256:
+    split-BF16 x6 by default, 3xTF32 with mode 3): algorithmic bytes (FP64
+    time slices in, complex FP32 Hermitian half out, or the reverse) and
+    tensor flops as issued (six, or three, 128 x npad x 32 MMA products per
+    tile and reduction chunk).  The TF32 fraction is of half the BF16 peak
+    (the dense TF32 rate is half the BF16 rate)."""
     K, J, nblk = sizes.n_t, sizes.J, sizes.n_blk
     npad = (K + 15) // 16 * 16
     tiles = (nblk + 127) // 128
     red = {"dft_fwd": (K + 31) // 32 * 32, "dft_inv": (2 * J + 31) // 32 * 32}
     nbytes = K * nblk * 8 + J * nblk * 8
-    out = {"mode": "bf16x6 tcgen05" if K <= 256 else "simt", "bytes_per_launch": nbytes}
+    tf32 = mode == 3
+    nprod = 3 if tf32 else 6
+    peak = bf16_peak[0] / 2 if tf32 else bf16_peak[0]
+    out = {"mode": ("tf32x3 tcgen05" if tf32 else "bf16x6 tcgen05") if K <= 256 else "simt",
+           "bytes_per_launch": nbytes}
     for d, c in dft.items():
         if not c["timed"]:
             continue
         ms = c["ms"] / c["timed"]
-        fl = 6 * 2 * 128 * npad * red[d] * tiles
+        fl = nprod * 2 * 128 * npad * red[d] * tiles
         out[d] = {"avg_ms": round(ms, 4), "GBps": round(nbytes / (ms / 1e3) / 1e9, 1),
                   "tensor_tflops_issued": round(fl / (ms / 1e3) / 1e12, 1),
-                  "tensor_frac_of_bf16_peak": round(fl / (ms / 1e3) / 1e12 / bf16_peak[0], 4)}
-    out["bf16_peak_tflops"] = bf16_peak[0]
-    out["bf16_peak_source"] = bf16_peak[1]
+                  "tensor_frac_of_peak": round(fl / (ms / 1e3) / 1e12 / peak, 4)}
+    out["peak_tflops"] = peak
+    out["peak_source"] = bf16_peak[1] + (" BF16 rate / 2 for TF32" if tf32 else "")
     return out
 
 
@@ -278,8 +289,10 @@ def run_ours(a):
 
     def make(beta, prec, seed):
         p = binding.default_params(kind=W["kind"], level=W["level"], n_t=K, tau=tau, beta=beta, nu=W["nu"],
-                                   x0=W["x0"], x1=W["x1"], wind=W["wind"], prec=prec, inner_maxit=a.inner_maxit,
-                                   outer_restart=a.outer_restart or W.get("restart", 30))
+                                   x0=W["x0"], x1=W["x1"], wind=W["wind"], prec=prec,
+                                   inner_maxit=W.get("inner_maxit", a.inner_maxit),
+                                   outer_restart=a.outer_restart or W.get("restart", 30),
+                                   dft_mode=W.get("dft_mode", 0) if prec else 0)
         G = binding.Problem(p, stream=stream.cuda_stream)
         vd = inputs.desired_state(N, W["x0"], W["x1"], K, tau, T, seed)
         G.set_data(vd)
@@ -407,7 +420,7 @@ def run_ours(a):
     traffic = profiled_traffic("mg_q2b_kernel_stokes64_nt256.md", "k_mg.cu") if a.workload == "stokes64_nt256" \
         else None
 
-    dft_line = dft_report(probs[0][0].sizes, dft, peaks_bf16())
+    dft_line = dft_report(probs[0][0].sizes, dft, peaks_bf16(), W.get("dft_mode", 0))
 
     line = {
         "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": ws, "steps": a.steps,
@@ -452,8 +465,11 @@ def serve_requests(seed, count, max_level):
     """The serving stream's requests, drawn from default_rng(seed) in this
     order per request: kind 50/50; N in {16, 32, 64, 128} (levels 4..7, capped
     at max_level; Oseen requests drawn at 16x16 run at 32x32); n_t in
-    {16, 32, 64, 128, 256}; log10 beta ~ U[-6, -2] (capped at 1e-4 for
-    Oseen); nu in {1/50, 1/100} for Oseen (1e-2 for Stokes); a data seed."""
+    {16, 32, 64, 128, 256}; log10 beta ~ U[-6, -2]; nu in {1/50, 1/100} for
+    Oseen (1e-2 for Stokes); a data seed.  Oseen requests with beta > 1e-4
+    damp the SOR of their convection multigrids (sor_omega_conv = 0.5: with
+    omega = 1 the multigrid of the convection-dominated low-frequency Q_j
+    diverges there)."""
     rng = np.random.default_rng(seed)
     out = []
     for _ in range(count):
@@ -463,13 +479,13 @@ def serve_requests(seed, count, max_level):
         beta = float(10.0 ** rng.uniform(-6.0, -2.0))
         nu = float(rng.choice([1 / 50, 1 / 100])) if oseen else 1e-2
         dseed = int(rng.integers(0, 2 ** 31))
+        omega_conv = 0.0
         if oseen:
             # 16x16 Oseen: the Uzawa/commutator inner solver stagnates (inner GMRES at its cap)
             level = max(level, 5)
-            # beta > 1e-4: the SOR multigrid for the convection-dominated Q_j of the lowest
-            # frequencies (mass shift tau/sqrt(beta) only) does not converge and Uzawa diverges
-            beta = min(beta, 1e-4)
-        out.append(dict(oseen=oseen, level=min(level, max_level), K=K, beta=beta, nu=nu, seed=dseed))
+            omega_conv = 0.5 if beta > 1e-4 else 0.0
+        out.append(dict(oseen=oseen, level=min(level, max_level), K=K, beta=beta, nu=nu, seed=dseed,
+                        omega_conv=omega_conv))
     return out
 
 
@@ -485,12 +501,13 @@ def run_serve(a):
         x0, x1 = (-1.0, 1.0) if r["oseen"] else (0.0, 1.0)
         tau = 1.0 / (r["K"] + 1)
         p = binding.default_params(kind=int(r["oseen"]), level=r["level"], n_t=r["K"], tau=tau, beta=r["beta"],
-                                   nu=r["nu"], x0=x0, x1=x1, wind=int(r["oseen"]), prec=a.serve_prec)
+                                   nu=r["nu"], x0=x0, x1=x1, wind=int(r["oseen"]), prec=a.serve_prec,
+                                   sor_omega_conv=r["omega_conv"])
         vd = inputs.desired_state(2 ** r["level"], x0, x1, r["K"], tau, 1.0, seed=r["seed"])
         n = r["K"] * (4 * (2 ** (r["level"] + 1) + 1) ** 2 + 2 * (2 ** r["level"] + 1) ** 2)
         built.append((p, vd, n))
     torch.cuda.synchronize()
-    srv = binding.Server(max_active=a.slots)
+    srv = binding.Server(max_active=a.slots, share_solves=bool(a.share))
     clk = Clocks(0)
     clk.start()
     t0 = time.perf_counter()
@@ -516,6 +533,9 @@ def run_serve(a):
             "latency_ms": {"p50": round(float(np.percentile(lat, 50)), 1),
                            "p99": round(float(np.percentile(lat, 99)), 1)},
             "requests": len(ids), "failed": fails, "arrival_rate": a.rate, "slots": a.slots,
+            "shared_solves": {"on": bool(a.share), "batches": st["shared_batches"],
+                              "member_applies": st["shared_member_solves"],
+                              "frequencies": st["shared_frequencies"], "largest_batch": st["shared_max_members"]},
             "active_peak": st["active_peak"], "bytes_peak": st["bytes_peak"], "budget_bytes": st["budget_bytes"],
             "outer_iterations": its, "wall_s": round(wall, 2),
             "config": {"workload": "serve", "seed": a.seed, "max_level": a.max_level,

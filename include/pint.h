@@ -359,12 +359,27 @@ typedef struct pint_server_s* pint_server;
 typedef struct {
   size_t device_budget; /* bytes admitted requests may hold; 0: 90% of free memory */
   int max_active;       /* worker slots (requests on the GPU at once), 1..64      */
+  /* 1: batch the frequency solves of the requests on the GPU.  Requests that
+   * share grid level, domain, wind, nu, precision and the inner-solver
+   * settings form a group; each keeps its own outer FGMRES, KKT matvec and
+   * time DFT, and the frequency solves of the members that need a
+   * preconditioner apply at about the same time (a batch waits at most 3 ms
+   * for members still in their outer step) run in shared launches over all
+   * their frequencies, each frequency with its own problem's constants.  The
+   * frequencies are independent (Sec. 3.1): every result is the same as in a
+   * solve alone.  Admission then counts each request's share of its group's
+   * shared workspace.  0: every request solves on its own handle. */
+  int share_solves;
 } pint_server_params;
 
 typedef struct {
   long long submitted, completed, failed, active, queued;
   size_t budget_bytes, bytes_in_use, bytes_peak; /* by estimate               */
   int active_peak;                               /* most requests at once     */
+  /* shared frequency solves (share_solves = 1): batches run, member applies
+   * they served (sum of batch sizes), frequencies solved, largest batch */
+  long long shared_batches, shared_member_solves, shared_frequencies;
+  int shared_max_members;
 } pint_server_stats;
 
 /* Start the worker threads.  PINT_ERR_ARG for max_active outside [1, 64]. */

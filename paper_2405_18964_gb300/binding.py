@@ -64,13 +64,15 @@ class Profile(ctypes.Structure):
 _lib = None
 _P = ctypes.c_void_p
 class ServerParams(ctypes.Structure):
-    _fields_ = [("device_budget", ctypes.c_size_t), ("max_active", ctypes.c_int)]
+    _fields_ = [("device_budget", ctypes.c_size_t), ("max_active", ctypes.c_int), ("share_solves", ctypes.c_int)]
 
 
 class ServerStats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_longlong), ("completed", ctypes.c_longlong), ("failed", ctypes.c_longlong),
                 ("active", ctypes.c_longlong), ("queued", ctypes.c_longlong), ("budget_bytes", ctypes.c_size_t),
-                ("bytes_in_use", ctypes.c_size_t), ("bytes_peak", ctypes.c_size_t), ("active_peak", ctypes.c_int)]
+                ("bytes_in_use", ctypes.c_size_t), ("bytes_peak", ctypes.c_size_t), ("active_peak", ctypes.c_int),
+                ("shared_batches", ctypes.c_longlong), ("shared_member_solves", ctypes.c_longlong),
+                ("shared_frequencies", ctypes.c_longlong), ("shared_max_members", ctypes.c_int)]
 
 
 _SIGS = {
@@ -367,8 +369,8 @@ class Server:
     """Serving loop (pint_server_*): continuous batching of control problems
     on the current device; see include/pint.h."""
 
-    def __init__(self, max_active=4, device_budget=0):
-        sp = ServerParams(device_budget, max_active)
+    def __init__(self, max_active=4, device_budget=0, share_solves=False):
+        sp = ServerParams(device_budget, max_active, 1 if share_solves else 0)
         h = ctypes.c_void_p()
         code = lib().pint_server_create(ctypes.byref(sp), ctypes.byref(h))
         if code != 0:
@@ -412,3 +414,10 @@ class Server:
         if self.h:
             lib().pint_server_destroy(self.h)
             self.h = None
+
+    def __del__(self):
+        # finish the workers before the interpreter tears down the CUDA context
+        try:
+            self.close()
+        except Exception:
+            pass

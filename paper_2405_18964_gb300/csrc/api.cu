@@ -45,6 +45,13 @@ struct Status {
 
 struct pint_ctx;
 
+// One frequency of a context's frequency-domain solve: the problem it comes
+// from (tau, beta, number of time blocks K) and its index j <= K/2.
+struct FreqDesc {
+  double tau, beta;
+  int K, j;
+};
+
 template <class T>
 struct Engine {
   pint_ctx* c = nullptr;
@@ -90,6 +97,14 @@ struct pint_ctx {
   Slots s{};
   bool oseen = false, conv = false, fp32 = false;
   double omega_conv = 1.0;                // SOR relaxation of the Q_j, Q_j^H multigrids (Oseen)
+  // Role in the serving loop's shared frequency solves: 0 = ordinary handle;
+  // 1 = member (time-domain parts and the frequency vectors of its DFT only;
+  // its frequency solves run in a shared context); 2 = shared frequency-domain
+  // context for up to `role_cap` frequencies (no DFT, no outer FGMRES).
+  int role = 0, role_cap = 0;
+  struct BatchGroup* group = nullptr;     // role 1: the shared context's group
+  bool in_solve = false;
+  pint_status batch_rc = PINT_OK;         // role 1: status of the last shared frequency solve
   bool gwind = false;                     // conv by node stencils (two-vortex or nodal wind), not separable
   std::vector<double> wind_nodal;         // PINT_WIND_NODAL: [2][n_s] values at the finest Q2 nodes
   double* nst64[PINT_MAXLEV] = {};        // node-order FP64 Q2 convection stencils per level (gwind)
@@ -114,6 +129,9 @@ struct pint_ctx {
   double* d_one = nullptr;    // [J] complex 1
   double* d_invtau = nullptr; // [J] complex 1/tau
   double* d_mtaumu = nullptr; // [J] complex -tau/mu
+  double* d_negtau = nullptr; // [J] -tau
+  int *d_space = nullptr, *d_conv = nullptr, *d_status = nullptr;  // coarse setup per op
+  int jcap = 0;               // frequencies the per-frequency tables and jobs are allocated for
   OpCoef *d_cuza = nullptr, *d_cuzd = nullptr, *d_cmass = nullptr, *d_cxp = nullptr;
   FieldJob *j_W4 = nullptr, *j_Q2 = nullptr, *j_QH2 = nullptr, *j_M2 = nullptr, *j_Kp2 = nullptr,
            *j_Mp2 = nullptr, *j_Kp2s = nullptr, *j_Mp2s = nullptr, *j_one = nullptr;
@@ -437,6 +455,7 @@ void Engine<T>::block_prec(const cpx<T>* U, cpx<T>* Out, const int* active) {
   br.s = s;
   br.J = J;
   br.c = -c->p.tau;
+  br.cj = c->d_negtau;  // -tau of each frequency's problem
   br.out0 = s.p;
   br.z0 = s.p;
   br.vel0 = s.lx;
@@ -604,10 +623,18 @@ void dft_inverse_any<float>(pint_ctx* c, Engine<float>& e, const cpx<float>* X, 
     launch_dft_inverse<float>(c->K, c->J, c->s.nblk, X, y, e.cosk, e.sink, c->st);
 }
 
+// The frequency solves of a member of the serving loop's shared solves
+// (role 1), run together with those of the other members in a shared
+// context; defined with the serving support below.
+pint_status shared_freq_solve(pint_ctx* c, void* R, void* Y, int* its_host);
+
 template <class T>
 void Engine<T>::apply(const double* r, double* z, int* its_host) {
   dft_forward_any<T>(c, *this, r, R);
-  freq_solve(R, Y, its_host);
+  if (c->role == 1)
+    c->batch_rc = shared_freq_solve(c, R, Y, its_host);
+  else
+    freq_solve(R, Y, its_host);
   dft_inverse_any<T>(c, *this, Y, z);
 }
 
@@ -663,8 +690,18 @@ bool setup_engine(pint_ctx* c, Engine<T>& e, size_t mg_jobs_q2, size_t mg_jobs_q
   e.c = c;
   e.tabs = tabs_of<T>(c);
   const size_t fv = (size_t)c->J * c->s.nblk;
-  if (!c->alloc(&e.R, fv * sizeof(cpx<T>)) || !c->alloc(&e.Y, fv * sizeof(cpx<T>)) ||
-      !c->alloc(&e.T1, fv * sizeof(cpx<T>)) || !c->alloc(&e.T2, fv * sizeof(cpx<T>)) ||
+  if (!c->alloc(&e.R, fv * sizeof(cpx<T>)) || !c->alloc(&e.Y, fv * sizeof(cpx<T>))) return false;
+  if (c->role == 1) {
+    // a member of the shared frequency solves: the DFT's input and output only
+    std::vector<T> cs(c->K), sn(c->K);
+    for (int k = 0; k < c->K; ++k) {
+      const double a = 2.0 * M_PI * (double)k / (double)c->K;
+      cs[k] = (T)std::cos(a);
+      sn[k] = (T)std::sin(a);
+    }
+    return c->upload(&e.cosk, cs) && c->upload(&e.sink, sn);
+  }
+  if (!c->alloc(&e.T1, fv * sizeof(cpx<T>)) || !c->alloc(&e.T2, fv * sizeof(cpx<T>)) ||
       !c->alloc(&e.T3, fv * sizeof(cpx<T>)))
     return false;
   if (!c->p.linear) {
@@ -751,11 +788,185 @@ void level_convection_stencils(const pint_params& p, const double* wind, int l, 
   }
 }
 
+// ---------------------------------------------------------------------------
+// Per-frequency tables.  A context's frequency-domain solve runs over a list
+// of frequencies, each from a problem with its own tau, beta and number of
+// time blocks K (one problem for a handle; several for the shared solve of
+// the serving loop, whose members share grid, wind, nu and solver settings).
+// The tables are allocated for `cap` frequencies once and refilled.
+// ---------------------------------------------------------------------------
+bool alloc_freq_tables(pint_ctx* c, int cap) {
+  const size_t nops = 2 * (size_t)cap + 3;
+  bool ok = c->alloc(&c->d_ops, sizeof(OpCoef) * nops) && c->alloc(&c->d_space, sizeof(int) * nops) &&
+            c->alloc(&c->d_conv, sizeof(int) * nops) && c->alloc(&c->d_status, sizeof(int) * nops) &&
+            c->alloc(&c->d_cinv, sizeof(double) * 2 * PINT_NC_MAX * PINT_NC_MAX * nops) &&
+            c->alloc(&c->d_blkZ, sizeof(BlkCoef) * cap) && c->alloc(&c->d_blkG, sizeof(BlkCoef) * cap) &&
+            c->alloc(&c->d_tc, sizeof(double) * 3 * cap) && c->alloc(&c->d_sa, sizeof(double) * 2 * cap) &&
+            c->alloc(&c->d_sb, sizeof(double) * 2 * cap) && c->alloc(&c->d_one, sizeof(double) * 2 * cap) &&
+            c->alloc(&c->d_invtau, sizeof(double) * 2 * cap) && c->alloc(&c->d_mtaumu, sizeof(double) * 2 * cap) &&
+            c->alloc(&c->d_negtau, sizeof(double) * cap) && c->alloc(&c->d_cuza, sizeof(OpCoef) * 3 * cap) &&
+            c->alloc(&c->d_cuzd, sizeof(OpCoef) * 3 * cap) && c->alloc(&c->d_cmass, sizeof(OpCoef) * 2 * cap) &&
+            c->alloc(&c->d_cxp, sizeof(OpCoef) * 5 * cap);
+  const size_t fj = sizeof(FieldJob);
+  if (!c->oseen)
+    ok = ok && c->alloc(&c->j_W4, fj * 4 * cap) && c->alloc(&c->j_Kp2, fj * 2 * cap) &&
+         c->alloc(&c->j_Mp2, fj * cap);
+  else
+    ok = ok && c->alloc(&c->j_Q2, fj * 2 * cap) && c->alloc(&c->j_QH2, fj * 2 * cap) &&
+         c->alloc(&c->j_M2, fj * cap) && c->alloc(&c->j_Kp2s, fj * 2 * cap) && c->alloc(&c->j_Mp2s, fj * cap);
+  ok = ok && c->alloc(&c->j_one, fj) && c->alloc(&c->d_active_one, sizeof(int) * cap);
+  c->jcap = cap;
+  return ok;
+}
+
+template <class V>
+bool put(pint_ctx* c, V* dst, const std::vector<V>& src) {
+  return c->cu(cudaMemcpyAsync(dst, src.data(), sizeof(V) * src.size(), cudaMemcpyHostToDevice, c->st), "tables");
+}
+
+pint_status fill_freq_tables(pint_ctx* c, const std::vector<FreqDesc>& fd) {
+  const int J = (int)fd.size();
+  if (J < 1 || J > c->jcap) return c->fail(PINT_ERR_ARG, "frequency list exceeds the context's capacity");
+  c->J = J;
+  c->gs.J = J;
+  const pint_params& p = c->p;
+  const Slots& s = c->s;
+  const double nu = p.nu, mu = p.uzawa_mu;
+  std::vector<double> dr(J), dc(J), c1(J), c2(J);
+  for (int j = 0; j < J; ++j) {
+    const double tau = fd[j].tau, beta = fd[j].beta;
+    const double th = 2.0 * M_PI * (double)fd[j].j / (double)fd[j].K;
+    dr[j] = 1.0 - std::cos(th);  // d_j = 1 - exp(-2 pi i j / K)
+    dc[j] = std::sin(th);
+    c1[j] = dr[j] / std::sqrt(tau * tau / beta + dc[j] * dc[j]);
+    c2[j] = 1.0 / std::sqrt(1.0 / beta + dc[j] * dc[j] / (tau * tau));
+  }
+  // operators: [0, J): W_j (Stokes) / Q_j (Oseen); [J, 2J): Q_j^H; 2J: K_p; 2J+1: M; 2J+2: M_p
+  c->nops = 2 * J + 3;
+  std::vector<OpCoef> ops(c->nops, OpCoef{0, 0, 0, 0});
+  std::vector<int> space(c->nops, 0), convf(c->nops, 0);
+  for (int j = 0; j < J; ++j) {
+    const double tau = fd[j].tau, sb = 1.0 / std::sqrt(fd[j].beta);
+    if (!c->oseen) {
+      ops[j] = OpCoef{1.0 + c1[j], 0.0, c2[j] * nu, 0.0};  // W_j = (1 + c1) M + c2 nu K
+      space[j] = 2;
+    } else {
+      // Q_j = d_j M + tau (nu K + N) + tau/sqrt(beta) M ; Q_j^H with N^T = -N
+      ops[j] = OpCoef{dr[j] + tau * sb, dc[j], tau * nu, tau};
+      ops[J + j] = OpCoef{dr[j] + tau * sb, -dc[j], tau * nu, -tau};
+      space[j] = space[J + j] = 2;
+      convf[j] = convf[J + j] = c->conv ? 1 : 0;
+    }
+  }
+  ops[2 * J] = OpCoef{0.0, 0.0, 1.0, 0.0};
+  space[2 * J] = 1;
+  ops[2 * J + 1] = OpCoef{1.0, 0.0, 0.0, 0.0};
+  ops[2 * J + 2] = OpCoef{1.0, 0.0, 0.0, 0.0};
+  if (!put(c, c->d_ops, ops) || !put(c, c->d_space, space) || !put(c, c->d_conv, convf) ||
+      !c->cu(cudaMemsetAsync(c->d_status, 0, sizeof(int) * c->nops, c->st), "coarse status"))
+    return PINT_ERR_CUDA;
+  launch_coarse_setup(c->t64, c->d_ops, c->d_space, c->d_conv, c->nops, c->d_cinv, c->d_status,
+                      c->gwind ? c->nst64[c->nlev - 1] : nullptr, c->st);
+  if (!c->launched("coarse setup")) return PINT_ERR_CUDA;
+
+  // frequency-block coefficients: G_j (Eq. SubBlockG) and Z_j (Eq. GJTransformation)
+  std::vector<BlkCoef> bz(J), bg(J);
+  std::vector<double> tc(3 * (size_t)J), sa(2 * (size_t)J), sbv(2 * (size_t)J), one(2 * (size_t)J),
+      invtau(2 * (size_t)J), mtaumu(2 * (size_t)J), negtau(J);
+  std::vector<OpCoef> cuza(3 * (size_t)J), cuzd(3 * (size_t)J), cmass(2 * (size_t)J), cxp(5 * (size_t)J);
+  for (int j = 0; j < J; ++j) {
+    const double tau = fd[j].tau, beta = fd[j].beta;
+    // a12 = conj(d_j), a21 = d_j with d_j = dr + i dc
+    bg[j] = BlkCoef{tau, 0, dr[j], -dc[j], dr[j], dc[j], -tau / beta, 0, tau, tau, tau, 0};
+    bz[j] = c->oseen ? bg[j] : BlkCoef{1, 0, c1[j], 0, c1[j], 0, -1, 0, c2[j], c2[j], 1, 0};
+    tc[3 * j] = std::sqrt(tau);
+    tc[3 * j + 1] = dc[j];
+    tc[3 * j + 2] = c2[j];
+    sa[2 * j] = 1.0 + c1[j];
+    sa[2 * j + 1] = 0;
+    sbv[2 * j] = nu * c2[j];
+    sbv[2 * j + 1] = 0;
+    one[2 * j] = 1.0;
+    one[2 * j + 1] = 0.0;
+    invtau[2 * j] = 1.0 / tau;
+    invtau[2 * j + 1] = 0.0;
+    mtaumu[2 * j] = -tau / mu;
+    mtaumu[2 * j + 1] = 0.0;
+    negtau[j] = -tau;
+    // Oseen combination coefficients
+    // T1[v] = 1 b1 + (-tau M) x1 + (-(conj d) M - tau nu K + tau N) x2
+    cuza[3 * j + 0] = OpCoef{1, 0, 0, 0};
+    cuza[3 * j + 1] = OpCoef{-tau, 0, 0, 0};
+    cuza[3 * j + 2] = OpCoef{-dr[j], dc[j], -tau * nu, tau};
+    // T1[lam] = 1 b2 + (-d M - tau nu K - tau N) x1 + (tau/beta M) x2
+    cuzd[3 * j + 0] = OpCoef{1, 0, 0, 0};
+    cuzd[3 * j + 1] = OpCoef{-dr[j], -dc[j], -tau * nu, -tau};
+    cuzd[3 * j + 2] = OpCoef{tau / beta, 0, 0, 0};
+    cmass[2 * j + 0] = OpCoef{0, 0, 0, 0};
+    cmass[2 * j + 1] = OpCoef{1, 0, 0, 0};
+    // T3[p] = -(1/tau^2) [tau M_p a + (conj(d) M_p + tau nu K_p - tau N_p) b]
+    // T3[mu] = -(1/tau^2) [(d M_p + tau nu K_p + tau N_p) a - tau/beta M_p b]
+    const double it2 = 1.0 / (tau * tau);
+    cxp[5 * j + 0] = OpCoef{0, 0, 0, 0};
+    cxp[5 * j + 1] = OpCoef{-1.0 / tau, 0, 0, 0};
+    cxp[5 * j + 2] = OpCoef{-dr[j] * it2, dc[j] * it2, -nu / tau, 1.0 / tau};
+    cxp[5 * j + 3] = OpCoef{-dr[j] * it2, -dc[j] * it2, -nu / tau, -1.0 / tau};
+    cxp[5 * j + 4] = OpCoef{1.0 / (beta * tau), 0, 0, 0};
+  }
+  if (!put(c, c->d_blkZ, bz) || !put(c, c->d_blkG, bg) || !put(c, c->d_tc, tc) || !put(c, c->d_sa, sa) ||
+      !put(c, c->d_sb, sbv) || !put(c, c->d_one, one) || !put(c, c->d_invtau, invtau) ||
+      !put(c, c->d_mtaumu, mtaumu) || !put(c, c->d_negtau, negtau) || !put(c, c->d_cuza, cuza) ||
+      !put(c, c->d_cuzd, cuzd) || !put(c, c->d_cmass, cmass) || !put(c, c->d_cxp, cxp))
+    return PINT_ERR_CUDA;
+
+  // ---- job tables: each job the (x slot, b slot) pairs of one frequency sharing one operator
+  using SlotPairs = std::vector<std::pair<long long, long long>>;
+  auto jobs = [&](std::vector<SlotPairs> groups, int opbase, bool per_j_op) {
+    std::vector<FieldJob> v;
+    for (int j = 0; j < J; ++j)
+      for (auto& grp : groups) {
+        FieldJob jb{};
+        jb.nf = (int)grp.size();
+        for (int f = 0; f < jb.nf; ++f) {
+          jb.x_off[f] = (long long)j * s.nblk + grp[f].first;
+          jb.b_off[f] = (long long)j * s.nblk + grp[f].second;
+        }
+        jb.op = per_j_op ? opbase + j : opbase;
+        jb.freq = j;
+        v.push_back(jb);
+      }
+    return v;
+  };
+  bool ok = true;
+  if (!c->oseen) {
+    ok = put(c, c->j_W4, jobs({{{s.vx, s.vx}}, {{s.vy, s.vy}}, {{s.lx, s.lx}}, {{s.ly, s.ly}}}, 0, true)) &&
+         put(c, c->j_Kp2, jobs({{{s.p, s.p}}, {{s.mu, s.mu}}}, 2 * J, false)) &&
+         put(c, c->j_Mp2, jobs({{{s.p, s.p}, {s.mu, s.mu}}}, 2 * J + 2, false));
+  } else {
+    ok = put(c, c->j_Q2, jobs({{{s.lx, s.lx}}, {{s.ly, s.ly}}}, 0, true)) &&
+         put(c, c->j_QH2, jobs({{{s.lx, s.lx}}, {{s.ly, s.ly}}}, J, true)) &&
+         put(c, c->j_M2, jobs({{{s.vx, s.vx}, {s.vy, s.vy}}}, 2 * J + 1, false)) &&
+         put(c, c->j_Kp2s, jobs({{{s.p, s.mu}}, {{s.mu, s.p}}}, 2 * J, false)) &&
+         put(c, c->j_Mp2s, jobs({{{s.p, s.mu}, {s.mu, s.p}}}, 2 * J + 2, false));
+  }
+  if (!ok) return PINT_ERR_CUDA;
+  {
+    std::vector<int> st_h(c->nops);
+    if (!c->cu(cudaMemcpyAsync(st_h.data(), c->d_status, sizeof(int) * c->nops, cudaMemcpyDeviceToHost, c->st),
+               "coarse status") ||
+        !c->cu(cudaStreamSynchronize(c->st), "coarse setup"))
+      return PINT_ERR_CUDA;
+    for (int o = 0; o < c->nops; ++o)
+      if (st_h[o] != 0) return c->fail(PINT_ERR_ARG, "coarse-grid operator is singular or too large");
+  }
+  return PINT_OK;
+}
+
 pint_status build(pint_ctx* c) {
   const pint_params& p = c->p;
   c->N = 1 << p.level;
   c->K = p.n_t;
-  c->J = p.n_t / 2 + 1;
+  c->J = c->role == 2 ? c->role_cap : p.n_t / 2 + 1;
   c->nlev = p.level;  // grids N, N/2, ..., 2
   c->oseen = p.kind == PINT_OSEEN;
   c->conv = p.wind != PINT_WIND_NONE;
@@ -820,135 +1031,18 @@ pint_status build(pint_ctx* c) {
         return c->fail(PINT_ERR_OOM, "device allocation failed (convection stencils)");
     }
 
-  // ---- per-frequency constants (Sec. 3.1-3.2, Sec. 4)
-  const double tau = p.tau, beta = p.beta, nu = p.nu, mu = p.uzawa_mu;
-  std::vector<double> dr(J), dc(J), c1(J), c2(J);
-  for (int j = 0; j < J; ++j) {
-    const double th = 2.0 * M_PI * (double)j / (double)c->K;
-    dr[j] = 1.0 - std::cos(th);  // d_j = 1 - exp(-2 pi i j / K)
-    dc[j] = std::sin(th);
-    c1[j] = dr[j] / std::sqrt(tau * tau / beta + dc[j] * dc[j]);
-    c2[j] = 1.0 / std::sqrt(1.0 / beta + dc[j] * dc[j] / (tau * tau));
-  }
-  // operators: [0, J): W_j (Stokes) / Q_j (Oseen); [J, 2J): Q_j^H; 2J: K_p; 2J+1: M; 2J+2: M_p
-  c->nops = 2 * J + 3;
-  std::vector<OpCoef> ops(c->nops, OpCoef{0, 0, 0, 0});
-  std::vector<int> space(c->nops, 0), convf(c->nops, 0);
-  const double sb = 1.0 / std::sqrt(beta);
-  for (int j = 0; j < J; ++j) {
-    if (!c->oseen) {
-      ops[j] = OpCoef{1.0 + c1[j], 0.0, c2[j] * nu, 0.0};  // W_j = (1 + c1) M + c2 nu K
-      space[j] = 2;
-    } else {
-      // Q_j = d_j M + tau (nu K + N) + tau/sqrt(beta) M ; Q_j^H with N^T = -N
-      ops[j] = OpCoef{dr[j] + tau * sb, dc[j], tau * nu, tau};
-      ops[J + j] = OpCoef{dr[j] + tau * sb, -dc[j], tau * nu, -tau};
-      space[j] = space[J + j] = 2;
-      convf[j] = convf[J + j] = c->conv ? 1 : 0;
+  // ---- per-frequency tables and job tables (Sec. 3.1-3.2, Sec. 4); a shared
+  // context fills them per batch, a member has none
+  if (c->role != 1) {
+    if (!alloc_freq_tables(c, J)) return c->fail(PINT_ERR_OOM, "device allocation failed (frequency tables)");
+    if (c->role == 0) {
+      std::vector<FreqDesc> fd(J);
+      for (int j = 0; j < J; ++j) fd[j] = FreqDesc{p.tau, p.beta, c->K, j};
+      const pint_status rc = fill_freq_tables(c, fd);
+      if (rc != PINT_OK) return rc;
     }
   }
-  ops[2 * J] = OpCoef{0.0, 0.0, 1.0, 0.0};
-  space[2 * J] = 1;
-  ops[2 * J + 1] = OpCoef{1.0, 0.0, 0.0, 0.0};
-  ops[2 * J + 2] = OpCoef{1.0, 0.0, 0.0, 0.0};
-  int *d_space, *d_conv, *d_status;
-  if (!c->upload(&c->d_ops, ops) || !c->upload(&d_space, space) || !c->upload(&d_conv, convf) ||
-      !c->alloc(&d_status, sizeof(int) * c->nops) ||
-      !c->alloc(&c->d_cinv, sizeof(double) * 2 * PINT_NC_MAX * PINT_NC_MAX * c->nops))
-    return c->fail(PINT_ERR_OOM, "device allocation failed (operators)");
-  cudaMemsetAsync(d_status, 0, sizeof(int) * c->nops, c->st);
-  launch_coarse_setup(c->t64, c->d_ops, d_space, d_conv, c->nops, c->d_cinv, d_status,
-                      c->gwind ? c->nst64[c->nlev - 1] : nullptr, c->st);
-  if (!c->launched("coarse setup")) return PINT_ERR_CUDA;
-  {
-    std::vector<int> st_h(c->nops);
-    if (!c->cu(cudaMemcpyAsync(st_h.data(), d_status, sizeof(int) * c->nops, cudaMemcpyDeviceToHost, c->st),
-               "coarse status") ||
-        !c->cu(cudaStreamSynchronize(c->st), "coarse setup"))
-      return PINT_ERR_CUDA;
-    for (int o = 0; o < c->nops; ++o)
-      if (st_h[o] != 0) return c->fail(PINT_ERR_ARG, "coarse-grid operator is singular or too large");
-  }
-
-  // frequency-block coefficients: G_j (Eq. SubBlockG) and Z_j (Eq. GJTransformation)
-  std::vector<BlkCoef> bz(J), bg(J);
-  for (int j = 0; j < J; ++j) {
-    // a12 = conj(d_j), a21 = d_j with d_j = dr + i dc
-    bg[j] = BlkCoef{tau, 0, dr[j], -dc[j], dr[j], dc[j], -tau / beta, 0, tau, tau, tau, 0};
-    bz[j] = c->oseen ? bg[j] : BlkCoef{1, 0, c1[j], 0, c1[j], 0, -1, 0, c2[j], c2[j], 1, 0};
-  }
-  std::vector<double> tc(3 * (size_t)J), sa(2 * (size_t)J), sbv(2 * (size_t)J);
-  for (int j = 0; j < J; ++j) {
-    tc[3 * j] = std::sqrt(tau);
-    tc[3 * j + 1] = dc[j];
-    tc[3 * j + 2] = c2[j];
-    sa[2 * j] = 1.0 + c1[j];
-    sa[2 * j + 1] = 0;
-    sbv[2 * j] = nu * c2[j];
-    sbv[2 * j + 1] = 0;
-  }
-  // Oseen combination coefficients (per frequency)
-  std::vector<OpCoef> cuza(3 * (size_t)J), cuzd(3 * (size_t)J), cmass(2 * (size_t)J), cxp(5 * (size_t)J);
-  for (int j = 0; j < J; ++j) {
-    // T1[v] = 1 b1 + (-tau M) x1 + (-(conj d) M - tau nu K + tau N) x2
-    cuza[3 * j + 0] = OpCoef{1, 0, 0, 0};
-    cuza[3 * j + 1] = OpCoef{-tau, 0, 0, 0};
-    cuza[3 * j + 2] = OpCoef{-dr[j], dc[j], -tau * nu, tau};
-    // T1[lam] = 1 b2 + (-d M - tau nu K - tau N) x1 + (tau/beta M) x2
-    cuzd[3 * j + 0] = OpCoef{1, 0, 0, 0};
-    cuzd[3 * j + 1] = OpCoef{-dr[j], -dc[j], -tau * nu, -tau};
-    cuzd[3 * j + 2] = OpCoef{tau / beta, 0, 0, 0};
-    cmass[2 * j + 0] = OpCoef{0, 0, 0, 0};
-    cmass[2 * j + 1] = OpCoef{1, 0, 0, 0};
-    // T3[p] = -(1/tau^2) [tau M_p a + (conj(d) M_p + tau nu K_p - tau N_p) b]
-    // T3[mu] = -(1/tau^2) [(d M_p + tau nu K_p + tau N_p) a - tau/beta M_p b]
-    const double it2 = 1.0 / (tau * tau);
-    cxp[5 * j + 0] = OpCoef{0, 0, 0, 0};
-    cxp[5 * j + 1] = OpCoef{-1.0 / tau, 0, 0, 0};
-    cxp[5 * j + 2] = OpCoef{-dr[j] * it2, dc[j] * it2, -nu / tau, 1.0 / tau};
-    cxp[5 * j + 3] = OpCoef{-dr[j] * it2, -dc[j] * it2, -nu / tau, -1.0 / tau};
-    cxp[5 * j + 4] = OpCoef{1.0 / (beta * tau), 0, 0, 0};
-  }
-  if (!c->upload(&c->d_blkZ, bz) || !c->upload(&c->d_blkG, bg) || !c->upload(&c->d_tc, tc) ||
-      !c->upload(&c->d_sa, sa) || !c->upload(&c->d_sb, sbv) || !c->upload(&c->d_one, cplx_table(J, 1, 0)) ||
-      !c->upload(&c->d_invtau, cplx_table(J, 1.0 / tau, 0)) ||
-      !c->upload(&c->d_mtaumu, cplx_table(J, -tau / mu, 0)) || !c->upload(&c->d_cuza, cuza) ||
-      !c->upload(&c->d_cuzd, cuzd) || !c->upload(&c->d_cmass, cmass) || !c->upload(&c->d_cxp, cxp))
-    return c->fail(PINT_ERR_OOM, "device allocation failed (coefficients)");
-
-  // ---- job tables
-  // each job: the (x slot, b slot) pairs of one frequency sharing one operator
-  using SlotPairs = std::vector<std::pair<long long, long long>>;
-  auto jobs = [&](std::vector<SlotPairs> groups, int opbase, bool per_j_op) {
-    std::vector<FieldJob> v;
-    for (int j = 0; j < J; ++j)
-      for (auto& grp : groups) {
-        FieldJob jb{};
-        jb.nf = (int)grp.size();
-        for (int f = 0; f < jb.nf; ++f) {
-          jb.x_off[f] = (long long)j * s.nblk + grp[f].first;
-          jb.b_off[f] = (long long)j * s.nblk + grp[f].second;
-        }
-        jb.op = per_j_op ? opbase + j : opbase;
-        jb.freq = j;
-        v.push_back(jb);
-      }
-    return v;
-  };
   bool ok = true;
-  if (!c->oseen) {
-    ok = ok && c->upload(&c->j_W4, jobs({{{s.vx, s.vx}}, {{s.vy, s.vy}}, {{s.lx, s.lx}}, {{s.ly, s.ly}}}, 0, true));
-    ok = ok && c->upload(&c->j_Kp2, jobs({{{s.p, s.p}}, {{s.mu, s.mu}}}, 2 * J, false));
-    ok = ok && c->upload(&c->j_Mp2, jobs({{{s.p, s.p}, {s.mu, s.mu}}}, 2 * J + 2, false));
-  } else {
-    ok = ok && c->upload(&c->j_Q2, jobs({{{s.lx, s.lx}}, {{s.ly, s.ly}}}, 0, true));
-    ok = ok && c->upload(&c->j_QH2, jobs({{{s.lx, s.lx}}, {{s.ly, s.ly}}}, J, true));
-    ok = ok && c->upload(&c->j_M2, jobs({{{s.vx, s.vx}, {s.vy, s.vy}}}, 2 * J + 1, false));
-    ok = ok && c->upload(&c->j_Kp2s, jobs({{{s.p, s.mu}}, {{s.mu, s.p}}}, 2 * J, false));
-    ok = ok && c->upload(&c->j_Mp2s, jobs({{{s.p, s.mu}, {s.mu, s.p}}}, 2 * J + 2, false));
-  }
-  ok = ok && c->alloc(&c->j_one, sizeof(FieldJob)) && c->alloc(&c->d_active_one, sizeof(int) * J);
-  if (!ok) return c->fail(PINT_ERR_OOM, "device allocation failed (jobs)");
 
   // ---- multigrid / Chebyshev workspaces
   c->lay2 = make_layout(c->nlev, N, 2);
@@ -962,7 +1056,7 @@ pint_status build(pint_ctx* c) {
   const size_t chq1 = 2 * (size_t)J;
 
   // ---- inner GMRES state
-  if (!p.linear) {
+  if (!p.linear && c->role != 1) {
     GmresState& G = c->gs;
     G.J = J;
     G.m = c->m_in;
@@ -982,6 +1076,12 @@ pint_status build(pint_ctx* c) {
   else
     ok = setup_engine<double>(c, c->e64, mgq2, mgq1, chq2, chq1);
   if (!ok) return c->fail(PINT_ERR_OOM, "device allocation failed (preconditioner workspace)");
+  if (c->role == 2) {
+    // shared frequency-domain context: no DFT, no outer FGMRES
+    if (!c->cu(cudaMallocHost(&c->h_count, sizeof(int)), "pinned host buffer")) return PINT_ERR_OOM;
+    if (!c->cu(cudaStreamSynchronize(c->st), "setup")) return PINT_ERR_CUDA;
+    return PINT_OK;
+  }
   {
     const int mode = p.dft_mode == PINT_DFT_AUTO ? (c->fp32 && c->K <= 256 ? PINT_DFT_BF16X6 : PINT_DFT_SIMT)
                                                  : p.dft_mode;
@@ -1135,6 +1235,11 @@ pint_status fgmres(pint_ctx* c, double* x, pint_solve_info* info) {
       auto a0 = now();
       apply_prec(c, Vi, Zi, its.data());
       cudaStreamSynchronize(st);
+      if (c->batch_rc != PINT_OK) {
+        inf.outer_iterations = total;
+        if (info) *info = inf;
+        return c->batch_rc;
+      }
       auto a1 = now();
       for (int j = 0; j < c->J; ++j) {
         inf.inner_iterations_total += its[j];
@@ -1925,4 +2030,255 @@ extern "C" pint_status pint_mg_apply_noalloc(pint_handle h, int which, int j, co
   if (j < 0 || j >= h->J) return h->fail(PINT_ERR_ARG, "frequency index out of range");
   return h->fp32 ? mg_noalloc_T<float>(h, h->e32, which, j, in, out)
                  : mg_noalloc_T<double>(h, h->e64, which, j, in, out);
+}
+
+// ============================================================================
+// Shared frequency solves for the serving loop (serve.cpp).
+//
+// Requests that share the grid, the domain, the wind, nu, the precision and
+// the inner-solver settings form a group; their handles are members (role
+// 1): each keeps its own outer FGMRES, KKT matvec and time DFT, while the
+// frequency solves of all members that need a preconditioner apply at about
+// the same time run as ONE batch in the group's shared context (role 2):
+// every multigrid, Chebyshev, block-matvec and Gram-Schmidt launch covers the
+// frequencies of all of them, each frequency with the constants of its own
+// problem (tau, beta, n_t).  The frequencies are independent (Sec. 3.1), so a
+// member's result does not depend on the other members of its batch.
+// ============================================================================
+#include <condition_variable>
+#include <map>
+
+#include "batch.h"
+
+struct BatchMember {
+  pint_ctx* c;
+  void* R;
+  void* Y;
+  int* its;
+  bool done;
+  pint_status rc;
+};
+
+struct BatchGroup {
+  pint_batcher_s* owner = nullptr;
+  pint_params tmpl{};
+  pint_ctx* b = nullptr;  // shared frequency-domain context (role 2), or null
+  cudaStream_t st = nullptr;
+  std::vector<BatchMember*> pending;
+  bool running = false;
+  int members = 0, in_solve = 0;
+};
+
+struct pint_batcher_s {
+  std::mutex mu;
+  std::condition_variable cv;
+  std::map<std::string, BatchGroup*> groups;
+  double window_ms = 3.0;  // how long a batch waits for members still in their outer step
+  pint_batch_stats stats{};
+};
+
+namespace {
+
+std::string group_key(const pint_params& p) {
+  char k[512];
+  snprintf(k, sizeof k, "%d|%d|%.17g|%.17g|%d|%.17g|%d|%.17g|%d|%d|%d|%d|%d|%d|%d|%.17g|%.17g|%.17g|%d", p.kind,
+           p.level, p.x0, p.x1, p.wind, p.nu, p.prec, p.inner_tol, p.inner_maxit, p.fixed_inner_its, p.mg_cycles,
+           p.mg_pre, p.mg_post, p.cheb_steps, p.uzawa_steps, p.uzawa_mu, p.sor_omega, p.sor_omega_conv, p.linear);
+  return k;
+}
+
+pint_status make_ctx(const pint_params& p, int role, int cap, void* stream, pint_ctx** out) {
+  pint_ctx* c = new (std::nothrow) pint_ctx();
+  if (!c) return PINT_ERR_OOM;
+  c->p = p;
+  c->role = role;
+  c->role_cap = cap;
+  c->st = static_cast<cudaStream_t>(stream);
+  const pint_status s = build(c);
+  if (s != PINT_OK) {
+    g_err = c->err;
+    free_ctx(c);
+    return s;
+  }
+  *out = c;
+  return PINT_OK;
+}
+
+// One batch: the frequencies of every member, solved in the group's shared
+// context (grown when the batch needs more frequencies than it holds).
+pint_status run_batch(BatchGroup* g, std::vector<BatchMember*>& batch) {
+  int jtot = 0;
+  for (BatchMember* m : batch) jtot += m->c->J;
+  if (!g->b || g->b->role_cap < jtot) {
+    if (g->b) {
+      free_ctx(g->b);
+      g->b = nullptr;
+    }
+    const pint_status rc = make_ctx(g->tmpl, 2, jtot, g->st, &g->b);
+    if (rc != PINT_OK) return rc;
+  }
+  pint_ctx* b = g->b;
+  std::vector<FreqDesc> fd;
+  fd.reserve(jtot);
+  for (BatchMember* m : batch)
+    for (int j = 0; j < m->c->J; ++j) fd.push_back(FreqDesc{m->c->p.tau, m->c->p.beta, m->c->K, j});
+  pint_status rc = fill_freq_tables(b, fd);
+  if (rc != PINT_OK) return rc;
+  const size_t cb = b->fp32 ? sizeof(cpx<float>) : sizeof(cpx<double>);
+  const size_t nb = (size_t)b->s.nblk;
+  char* Rb = static_cast<char*>(b->fp32 ? (void*)b->e32.R : (void*)b->e64.R);
+  char* Yb = static_cast<char*>(b->fp32 ? (void*)b->e32.Y : (void*)b->e64.Y);
+  size_t off = 0;
+  for (BatchMember* m : batch) {
+    const size_t bytes = (size_t)m->c->J * nb * cb;
+    if (!b->cu(cudaMemcpyAsync(Rb + off, m->R, bytes, cudaMemcpyDeviceToDevice, b->st), "batch input"))
+      return PINT_ERR_CUDA;
+    off += bytes;
+  }
+  std::vector<int> its(jtot, 0);
+  if (b->fp32)
+    b->e32.freq_solve(b->e32.R, b->e32.Y, its.data());
+  else
+    b->e64.freq_solve(b->e64.R, b->e64.Y, its.data());
+  off = 0;
+  int j0 = 0;
+  for (BatchMember* m : batch) {
+    const size_t bytes = (size_t)m->c->J * nb * cb;
+    if (!b->cu(cudaMemcpyAsync(m->Y, Yb + off, bytes, cudaMemcpyDeviceToDevice, b->st), "batch output"))
+      return PINT_ERR_CUDA;
+    if (m->its) std::copy(its.begin() + j0, its.begin() + j0 + m->c->J, m->its);
+    off += bytes;
+    j0 += m->c->J;
+  }
+  if (!b->launched("shared frequency solve") || !b->cu(cudaStreamSynchronize(b->st), "shared frequency solve"))
+    return PINT_ERR_CUDA;
+  return PINT_OK;
+}
+
+}  // namespace
+
+pint_status shared_freq_solve(pint_ctx* c, void* R, void* Y, int* its_host) {
+  BatchGroup* g = c->group;
+  pint_batcher_s* B = g->owner;
+  if (!c->cu(cudaStreamSynchronize(c->st), "member DFT")) return PINT_ERR_CUDA;
+  BatchMember me{c, R, Y, its_host, false, PINT_OK};
+  std::unique_lock<std::mutex> lk(B->mu);
+  g->pending.push_back(&me);
+  B->cv.notify_all();
+  while (!me.done) {
+    if (!g->running && !g->pending.empty()) {
+      // this thread runs the next batch (one batch of a group at a time):
+      // first wait (bounded) for the members that are still in their outer step
+      g->running = true;
+      const auto deadline = std::chrono::steady_clock::now() +
+                            std::chrono::microseconds((long long)(B->window_ms * 1000.0));
+      while ((int)g->pending.size() < g->in_solve && std::chrono::steady_clock::now() < deadline)
+        B->cv.wait_until(lk, deadline);
+      std::vector<BatchMember*> batch;
+      batch.swap(g->pending);
+      lk.unlock();
+      const pint_status rc = batch.empty() ? PINT_OK : run_batch(g, batch);
+      lk.lock();
+      int nf = 0;
+      for (BatchMember* m : batch) {
+        m->rc = rc;
+        m->done = true;
+        nf += m->c->J;
+      }
+      B->stats.batches++;
+      B->stats.member_solves += (long long)batch.size();
+      B->stats.frequencies += nf;
+      B->stats.max_members = std::max(B->stats.max_members, (int)batch.size());
+      if (rc != PINT_OK) c->err = g_err = "shared frequency solve failed: " + g_err;
+      g->running = false;
+      B->cv.notify_all();
+    } else {
+      B->cv.wait(lk);
+    }
+  }
+  return me.rc;
+}
+
+pint_batcher_s* batcher_create() { return new pint_batcher_s(); }
+
+void batcher_destroy(pint_batcher_s* B) {
+  if (!B) return;
+  for (auto& kv : B->groups) {
+    if (kv.second->b) free_ctx(kv.second->b);
+    if (kv.second->st) cudaStreamDestroy(kv.second->st);
+    delete kv.second;
+  }
+  delete B;
+}
+
+pint_status member_create(pint_batcher_s* B, const pint_params* p, void* stream, pint_handle* out) {
+  std::string why;
+  if (!valid_params(p, why)) return g_err = why, PINT_ERR_ARG;
+  if (p->wind == PINT_WIND_NODAL) return g_err = "shared solves take the built-in winds only", PINT_ERR_ARG;
+  pint_ctx* c = nullptr;
+  const pint_status rc = make_ctx(*p, 1, 0, stream, &c);
+  if (rc != PINT_OK) return rc;
+  std::lock_guard<std::mutex> lk(B->mu);
+  BatchGroup*& g = B->groups[group_key(*p)];
+  if (!g) {
+    g = new BatchGroup();
+    g->owner = B;
+    g->tmpl = *p;
+    cudaStreamCreateWithFlags(&g->st, cudaStreamNonBlocking);
+  }
+  g->members++;
+  c->group = g;
+  *out = c;
+  return PINT_OK;
+}
+
+void member_destroy(pint_handle h) {
+  if (!h) return;
+  BatchGroup* g = h->group;
+  if (g) {
+    std::lock_guard<std::mutex> lk(g->owner->mu);
+    if (--g->members == 0 && g->b && !g->running) {
+      free_ctx(g->b);  // the group's memory goes back with its last member
+      g->b = nullptr;
+    }
+  }
+  free_ctx(h);
+}
+
+void member_solve_begin(pint_handle h) {
+  std::lock_guard<std::mutex> lk(h->group->owner->mu);
+  h->group->in_solve++;
+  h->in_solve = true;
+}
+
+void member_solve_end(pint_handle h) {
+  std::lock_guard<std::mutex> lk(h->group->owner->mu);
+  h->group->in_solve--;
+  h->in_solve = false;
+  h->group->owner->cv.notify_all();
+}
+
+void batcher_get_stats(pint_batcher_s* B, pint_batch_stats* out) {
+  std::lock_guard<std::mutex> lk(B->mu);
+  *out = B->stats;
+}
+
+// Device bytes a member holds, and what one frequency adds to its group's
+// shared context (upper estimates, host arithmetic only).
+void shared_estimates(const pint_params* p, size_t* member_bytes, size_t* per_freq_bytes) {
+  const long long N = 1LL << p->level, K = p->n_t, J = K / 2 + 1;
+  const long long ns = (2 * N + 1) * (2 * N + 1), nq = (N + 1) * (N + 1), nblk = 4 * ns + 2 * nq;
+  const bool fp32 = p->prec == PINT_PREC_FP32, oseen = p->kind == PINT_OSEEN;
+  const long long cs = fp32 ? 8 : 16;
+  const long long m = p->outer_restart;
+  const long long m_in = p->fixed_inner_its > 0 ? p->fixed_inner_its : p->inner_maxit;
+  long long mb = (2 * m + 4) * K * nblk * 8 + J * nblk * 16 + 2 * J * nblk * cs;
+  *member_bytes = (size_t)(mb + mb / 20 + (64LL << 20));
+  long long f = 3 * nblk * cs;
+  if (!p->linear) f += (2 * m_in + 1) * nblk * cs + (m_in + 1) * m_in * 16 * 2;
+  const MGLayout l2 = make_layout(p->level, (int)N, 2), l1 = make_layout(p->level, (int)N, 1);
+  f += std::max((oseen ? 2 : 4) * l2.per_job, 2 * l1.per_job) * cs;
+  if (!oseen) f += 2 * l1.per_job * cs;
+  f += std::max((long long)(oseen ? 2 : 0) * 2 * ns, 2LL * 2 * nq) * cs;
+  *per_freq_bytes = (size_t)(f + f / 20);
 }

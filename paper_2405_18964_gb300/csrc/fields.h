@@ -80,6 +80,7 @@ struct BResArgs {
   Slots s;
   int J;
   double c;
+  const double* cj;  // per-frequency c (replaces c when set)
   long long out0, z0, vel0, out1, z1, vel1;
   const int* active;
   const cpx<T>* x;

@@ -346,7 +346,7 @@ __global__ void __launch_bounds__(TPB) bres_kernel(BResArgs<T> A) {
     O[A.out1 + t] = czero<T>();
     return;
   }
-  const T c = T(A.c);
+  const T c = T(A.cj ? A.cj[j] : A.c);
   cpx<T> r0 = Z[A.z0 + t], r1 = Z[A.z1 + t];
   rfma(r0, c, b_op<T>(A.tabs.bt, n1, n2, kx, ky, X + A.vel0, X + A.vel0 + A.s.ns));
   rfma(r1, c, b_op<T>(A.tabs.bt, n1, n2, kx, ky, X + A.vel1, X + A.vel1 + A.s.ns));

@@ -11,6 +11,12 @@
 // to the head of the queue while other requests are running (and fails only
 // when it cannot fit on an otherwise empty server).  Results, statuses and
 // latencies (submission to completion) are kept until collected.
+//
+// With share_solves, each request's handle is a member of a group (same grid,
+// domain, wind, nu, precision, inner-solver settings): its frequency solves
+// run batched with those of the other members in the group's shared context
+// (api.cu, batch.h), and admission counts the request's share of that
+// context.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -23,6 +29,7 @@
 #include <unordered_map>
 #include <vector>
 
+#include "batch.h"
 #include "pint.h"
 
 namespace {
@@ -60,6 +67,7 @@ struct pint_server_s {
   long long submitted = 0, completed = 0, failed = 0;
   bool stop = false;
   std::vector<std::thread> workers;
+  pint_batcher_s* batcher = nullptr;  // shared frequency solves (share_solves)
 
   void worker();
   bool run(Request* r, cudaStream_t st);
@@ -82,7 +90,7 @@ size_t ns_of(const pint_params& p) {
 // not be created for lack of device memory (the caller may retry later).
 bool pint_server_s::run(Request* r, cudaStream_t st) {
   pint_handle h = nullptr;
-  pint_status rc = pint_create(&r->p, st, &h);
+  pint_status rc = batcher ? member_create(batcher, &r->p, st, &h) : pint_create(&r->p, st, &h);
   if (rc == PINT_ERR_OOM) return false;
   if (rc != PINT_OK) {
     r->status = rc;
@@ -92,11 +100,16 @@ bool pint_server_s::run(Request* r, cudaStream_t st) {
   rc = pint_set_data(h, r->vd.data(), r->f.empty() ? nullptr : r->f.data(), r->v0.empty() ? nullptr : r->v0.data());
   if (rc == PINT_OK) {
     r->x.assign(r->kkt_len, 0.0);
+    if (batcher) member_solve_begin(h);
     rc = pint_solve_host(h, r->x.data(), &r->info);
+    if (batcher) member_solve_end(h);
   }
   if (rc != PINT_OK) r->msg = pint_last_error(h);
   r->status = rc;
-  pint_destroy(h);
+  if (batcher)
+    member_destroy(h);
+  else
+    pint_destroy(h);
   r->vd.clear();
   r->vd.shrink_to_fit();
   r->f.clear();
@@ -164,6 +177,7 @@ pint_status pint_server_create(const pint_server_params* sp, pint_server* out) {
   }
   s->budget = sp->device_budget ? std::min(sp->device_budget, free_b) : free_b / 10 * 9;
   s->max_active = sp->max_active;
+  if (sp->share_solves) s->batcher = batcher_create();
   for (int i = 0; i < s->max_active; ++i) s->workers.emplace_back([s] { s->worker(); });
   *out = s;
   return PINT_OK;
@@ -172,8 +186,14 @@ pint_status pint_server_create(const pint_server_params* sp, pint_server* out) {
 pint_status pint_server_submit(pint_server s, const pint_params* p, const double* vd, const double* f,
                                const double* v0, long long* id) {
   if (!s || !p || !vd || !id) return s_err = "null argument", PINT_ERR_ARG;
-  const size_t est = pint_estimate_device_bytes(p);
+  size_t est = pint_estimate_device_bytes(p);
   if (est == 0) return s_err = "invalid parameters", PINT_ERR_ARG;
+  if (s->batcher) {
+    // the member's own buffers plus its frequencies' share of the group's context
+    size_t mb = 0, pf = 0;
+    shared_estimates(p, &mb, &pf);
+    est = mb + (size_t)(p->n_t / 2 + 1) * pf;
+  }
   if (est > s->budget) return s_err = "request needs more device memory than the server's budget", PINT_ERR_OOM;
   Request* r = new Request();
   r->p = *p;
@@ -230,6 +250,12 @@ pint_status pint_server_get_stats(pint_server s, pint_server_stats* out) {
   out->bytes_in_use = s->in_use;
   out->bytes_peak = s->peak_bytes;
   out->active_peak = s->peak_active;
+  pint_batch_stats bs{};
+  if (s->batcher) batcher_get_stats(s->batcher, &bs);
+  out->shared_batches = bs.batches;
+  out->shared_member_solves = bs.member_solves;
+  out->shared_frequencies = bs.frequencies;
+  out->shared_max_members = bs.max_members;
   return PINT_OK;
 }
 
@@ -241,6 +267,7 @@ pint_status pint_server_destroy(pint_server s) {
     s->cv.notify_all();
   }
   for (auto& t : s->workers) t.join();
+  batcher_destroy(s->batcher);
   for (auto& kv : s->all) delete kv.second;
   delete s;
   return PINT_OK;

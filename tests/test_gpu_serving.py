@@ -96,3 +96,40 @@ def test_estimate_covers_the_handle(kind, level, K, prec):
     G.close()
     est = binding.estimate_device_bytes(p)
     assert actual <= est <= 1.25 * actual + (80 << 20), (actual, est)
+
+
+# requests sharing grid, domain, wind, nu and precision: two groups (Stokes
+# 16x16, Oseen 32x32) whose members differ in n_t and beta
+SHARED = [("stokes", 4, 16, 1e-2, 1e-2, 1, 11), ("stokes", 4, 8, 1e-4, 1e-2, 1, 12),
+          ("stokes", 4, 32, 1e-6, 1e-2, 1, 13), ("oseen", 5, 8, 1e-4, 1e-2, 1, 14),
+          ("oseen", 5, 16, 1e-5, 1e-2, 1, 15), ("stokes", 4, 16, 1e-3, 1e-2, 1, 16)]
+
+
+def test_shared_frequency_solves_same_as_alone():
+    """share_solves: the frequency solves of the requests on the GPU run in
+    shared launches; each result is bit for bit the one of the request
+    solved alone, and the batches did hold several requests."""
+    reqs = [_request(*m) for m in SHARED]
+    alone = []
+    for p, vd, n in reqs:
+        G = binding.Problem(p)
+        G.set_data(vd)
+        x = np.zeros(n)
+        info = G.solve_host(x)
+        G.close()
+        assert info.relres <= 1e-8
+        alone.append(x)
+    srv = binding.Server(max_active=6, share_solves=True)
+    try:
+        ids = [srv.submit(p, vd) for p, vd, _ in reqs]
+        got = [srv.wait(rid, n, check=False) for rid, (_, _, n) in zip(ids, reqs)]
+        st = srv.stats()
+    finally:
+        srv.close()
+    for k, (x, info, lat, code) in enumerate(got):
+        assert code == 0 and info.relres <= 1e-8, (k, code)
+        assert np.array_equal(x, alone[k]), (k, float(np.abs(x - alone[k]).max() / np.abs(alone[k]).max()))
+    print(f"shared solves: {st['shared_batches']} batches, {st['shared_member_solves']} member applies, "
+          f"largest batch {st['shared_max_members']} requests")
+    assert st["completed"] == len(SHARED) and st["failed"] == 0
+    assert st["shared_max_members"] >= 2 and st["shared_member_solves"] > st["shared_batches"]
