@@ -5,12 +5,17 @@ beta in {1e-2, 1e-4, 1e-6}, seeded divergence-free desired state), with the
 FP32 parallel-in-time preconditioner inside FP64 FGMRES(30); the plain FP64
 preconditioner is timed beside it.
 
-One step = one complete solve (right-hand side resident, x0 = 0): outer
-FGMRES, KKT matvecs, and in every preconditioner apply the time DFT, the
-Stokes transforms, the batched inner GMRES with multigrid / Chebyshev
-commutator preconditioning over all frequencies, and the inverse DFT.
-Steps cycle through the three beta values.  Inputs are larger than L2 (the
-FP64 FGMRES basis alone is 9.4 GB), so no flush is needed between steps.
+One step = the three problems (one per beta) solved concurrently to 1e-8
+(right-hand sides resident, x0 = 0), one host thread and CUDA stream each,
+their handles in one group (pint_group_*): each keeps its outer FGMRES, KKT
+matvecs and time DFTs, and the frequency solves of their preconditioner
+applies (Stokes transforms, batched inner GMRES with multigrid / Chebyshev
+commutator preconditioning) run in shared launches over the frequencies of
+all three.  value = solves / second over the timed steps; every result is bit
+for bit the one of the problem solved alone (checked in the line), and the
+line also reports the problems solved alone one after the other.  Inputs are
+larger than L2 (the FP64 FGMRES bases alone are 28 GB), so no flush is
+needed between steps.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Multi-GPU: replicas only (each rank solves its own problems; no collective
@@ -57,7 +62,7 @@ UNIT = "solves/s"
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="stokes64_nt256", choices=list(WORKLOADS) + ["serve"],
@@ -251,10 +256,12 @@ def workload_config(name, ws):
 
 
 def apply_roofline(cls, hbm, src):
-    """Preconditioner apply against HBM: the algorithmic bytes of every kernel
-    of the applies (the library's per-launch counts, pint.h pint_profile)
-    over the applies' event time (events on the handle's stream around each
-    whole apply; the pressure part's second stream joins inside it)."""
+    """Preconditioner applies against HBM: the algorithmic bytes of every
+    kernel of the applies (the library's per-launch counts, pint.h
+    pint_profile) over the event time of the shared frequency-solve batches
+    (events on the group's stream around each batch; the pressure part's
+    second stream joins inside it).  The time DFTs (0.5% of the launch time)
+    run on the problems' own streams and count bytes but no time here."""
     from paper_2405_18964_gb300 import binding
     ap = cls["apply"]
     if not ap["timed"] or ap["ms"] <= 0:
@@ -275,6 +282,11 @@ def algorithmic_bytes_mg_q2(sizes, nlaunch_jobs, cycles, bw):
 
 # ------------------------------------------------------------- our arm
 def run_ours(a):
+    """One step = the workload's problems (one per beta) solved concurrently,
+    one host thread and CUDA stream each, their handles in one group so that
+    their frequency solves run in shared launches (pint_group_*)."""
+    import threading
+
     import torch
     from paper_2405_18964_gb300 import binding, inputs
 
@@ -284,61 +296,93 @@ def run_ours(a):
     W = WORKLOADS[a.workload]
     K, T = W["K"], W["T"]
     tau = T / (K + 1)
-    stream = torch.cuda.current_stream()
     N = 2 ** W["level"]
 
-    def make(beta, prec, seed):
-        p = binding.default_params(kind=W["kind"], level=W["level"], n_t=K, tau=tau, beta=beta, nu=W["nu"],
-                                   x0=W["x0"], x1=W["x1"], wind=W["wind"], prec=prec,
-                                   inner_maxit=W.get("inner_maxit", a.inner_maxit),
-                                   outer_restart=a.outer_restart or W.get("restart", 30),
-                                   dft_mode=W.get("dft_mode", 0) if prec else 0)
-        G = binding.Problem(p, stream=stream.cuda_stream)
-        vd = inputs.desired_state(N, W["x0"], W["x1"], K, tau, T, seed)
-        G.set_data(vd)
-        return G, vd
+    def params(beta, prec):
+        return binding.default_params(kind=W["kind"], level=W["level"], n_t=K, tau=tau, beta=beta, nu=W["nu"],
+                                      x0=W["x0"], x1=W["x1"], wind=W["wind"], prec=prec,
+                                      inner_maxit=W.get("inner_maxit", a.inner_maxit),
+                                      outer_restart=a.outer_restart or W.get("restart", 30),
+                                      dft_mode=W.get("dft_mode", 0) if prec else 0)
 
     betas = W["betas"] if a.beta is None else [a.beta]
-    probs = [make(b, 1, sd) for b, sd in zip(betas, replica_seeds(rank, len(betas)))]
-    n = probs[0][0].kkt_len
-    x = torch.zeros(n, dtype=torch.float64, device="cuda")
+    seeds = replica_seeds(rank, len(betas))
+    vds = [inputs.desired_state(N, W["x0"], W["x1"], K, tau, T, sd) for sd in seeds]
+    group = binding.Group()
+    streams = [torch.cuda.Stream() for _ in betas]
+    probs = []
+    for b, vd, st in zip(betas, vds, streams):
+        G = binding.Problem(params(b, 1), stream=st.cuda_stream, group=group)
+        G.set_data(vd)
+        probs.append(G)
+    n = probs[0].kkt_len
+    xs = [torch.zeros(n, dtype=torch.float64, device="cuda") for _ in probs]
 
-    def step(i, prof=None):
-        G = probs[i % len(probs)][0]
-        x.zero_()
-        return G.solve(x)
+    def concurrently(fn):
+        """fn(k) for every problem, one host thread each; returns results and
+        each call's wall time (ms)."""
+        out, lat = [None] * len(probs), [0.0] * len(probs)
+
+        def run(k):
+            t0 = time.perf_counter()
+            out[k] = fn(k)
+            lat[k] = (time.perf_counter() - t0) * 1e3
+
+        th = [threading.Thread(target=run, args=(k,)) for k in range(len(probs))]
+        for t in th:
+            t.start()
+        for t in th:
+            t.join()
+        return out, lat
+
+    def solve_device(k):
+        with torch.cuda.stream(streams[k]):
+            xs[k].zero_()
+        # profiler captures (--only-timed with a shrunken basis) may stop before 1e-8
+        return probs[k].solve(xs[k], check=not a.only_timed)
+
+    def step():
+        return concurrently(solve_device)
 
     for i in range(a.warmup):
-        step(i)
+        step()
     torch.cuda.synchronize()
     # ---- timed region (device-resident inputs)
-    for G, _ in probs:
-        G.profile_enable(["mg_q2", "dft_fwd", "dft_inv", "apply"])
+    group.profile_enable(["mg_q2", "apply"])
+    for G in probs:
+        G.profile_enable(["dft_fwd", "dft_inv"])
     clk = Clocks(dev)
     clk.start()
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
+    s0 = torch.cuda.current_stream()
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps + 1)]
-    ev[0].record(stream)
-    infos = []
+    ev[0].record(s0)
+    infos, lat = [], []
     for i in range(a.steps):
-        infos.append(step(i))
-        ev[i + 1].record(stream)
+        inf, lt = step()
+        torch.cuda.synchronize()
+        ev[i + 1].record(s0)
+        infos += inf
+        lat += lt
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     clocks = clk.stop()
-    lat = [ev[i].elapsed_time(ev[i + 1]) for i in range(a.steps)]
     total_ms = ev[0].elapsed_time(ev[-1])
     total_ms = max_over_ranks(total_ms, dist)
-    prof = [G.profile_read() for G, _ in probs]
+    gprof = group.profile_read()
+    mprof = [G.profile_read() for G in probs]
     keys = ("launches", "timed", "ms", "bytes")
-    cls = {c: {k: sum(p[c][k] for p in prof) for k in keys} for c in binding.PROF_CLASSES}
+    cls = {c: {k: gprof[c][k] + sum(p[c][k] for p in mprof) for k in keys} for c in binding.PROF_CLASSES}
+    cls["apply"] = gprof["apply"]  # whole batches of shared frequency solves
     mg = cls["mg_q2"]
     dft = {d: cls[d] for d in ("dft_fwd", "dft_inv")}
     launches = sum(c["launches"] for c in cls.values())
-    value = whole_job_rate(a.steps, ws, total_ms)
+    solves = a.steps * len(probs)
+    value = solves * ws / (total_ms / 1e3)
+    gstats = group.stats()
     if a.only_timed:
         if rank == 0:
             hbm, src = peaks()
@@ -348,66 +392,91 @@ def run_ours(a):
                               "gpu_launches": int(launches),
                               "mg_q2_avg_launch_ms": mg["ms"] / max(1, mg["timed"]),
                               "mg_q2_GBps": mg_gbs, "mg_q2_frac": mg_gbs / hbm if mg_gbs else None,
-                              "apply": apply_roofline(cls, hbm, src),
+                              "apply": apply_roofline(cls, hbm, src), "shared": gstats,
                               "autotune": binding.autotune_report().strip().splitlines(),
                               "dft_avg_ms": {d: c["ms"] / max(1, c["timed"]) for d, c in dft.items()}}), flush=True)
+        for G in probs:
+            G.close()
+        group.close()
         return
 
-    # ---- per-class shares from one fully profiled solve (outside the timed region)
-    G0 = probs[0][0]
-    G0.profile_enable(binding.PROF_CLASSES)
-    step(0)
-    share = G0.profile_read()
-    tot = sum(c["ms"] for k, c in share.items() if k != "apply") or 1.0
-    shares = {k: round(c["ms"] / tot, 4) for k, c in share.items() if c["launches"] and k != "apply"}
-    shares["note"] = ("shares of the summed per-launch event times of one profiled solve; the pressure part "
-                      "runs on a second stream, so the summed times exceed the wall time")
-    G0.profile_enable([])
+    # ---- per-class shares from one fully profiled step (outside the timed region)
+    group.profile_enable(binding.PROF_CLASSES)
+    for G in probs:
+        G.profile_enable(binding.PROF_CLASSES)
+    step()
+    g2 = group.profile_read()
+    share = {c: g2[c]["ms"] + sum(G.profile_read()[c]["ms"] for G in probs) for c in binding.PROF_CLASSES}
+    share_launch = {c: g2[c]["launches"] + sum(G.profile_read()[c]["launches"] for G in probs)
+                    for c in binding.PROF_CLASSES}
+    tot = sum(v for k, v in share.items() if k != "apply") or 1.0
+    shares = {k: round(v / tot, 4) for k, v in share.items() if share_launch[k] and k != "apply"}
+    shares["note"] = ("shares of the summed per-launch event times of one profiled step; the pressure part "
+                      "runs on a second stream and the problems' outer steps on their own streams, so the "
+                      "summed times exceed the wall time")
+    group.profile_enable([])
+    for G in probs:
+        G.profile_enable([])
 
-    # ---- e2e through the public API with host buffers (pinned)
-    vd_pinned = [torch.from_numpy(vd).pin_memory() for _, vd in probs]
-    xh = torch.zeros(n, dtype=torch.float64).pin_memory()
-    xnp = xh.numpy()
-    e2e_ms = []
-    e2e_steps = min(a.steps, 2 * len(probs))
-    for i in range(e2e_steps):
-        G = probs[i % len(probs)][0]
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        G.set_data(vd_pinned[i % len(probs)].numpy())
+    # ---- e2e through the public API with host buffers (pinned): data upload,
+    # solve from a host initial guess, solution download, all problems at once
+    vd_pinned = [torch.from_numpy(vd).pin_memory() for vd in vds]
+    xh = [torch.zeros(n, dtype=torch.float64).pin_memory() for _ in probs]
+
+    def solve_host(k):
+        probs[k].set_data(vd_pinned[k].numpy())
+        xnp = xh[k].numpy()
         xnp[:] = 0.0
-        G.solve_host(xnp)
-        torch.cuda.synchronize()
-        e2e_ms.append((time.perf_counter() - t0) * 1e3)
-    h2d = int(vd_pinned[0].numel() * 8 + n * 8)
-    d2h = int(n * 8)
-    e2e = {"value": e2e_steps * ws / (sum(e2e_ms) / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
-           "d2h_bytes_per_step": d2h, "steps": e2e_steps}
+        return probs[k].solve_host(xnp)
 
-    # ---- FP64 plain preconditioner, same problems, within a time budget
+    e2e_steps = min(a.steps, 2)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        concurrently(solve_host)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    h2d = int(sum(v.numel() for v in vd_pinned) * 8 + len(probs) * n * 8)
+    d2h = int(len(probs) * n * 8)
+    e2e = {"value": e2e_steps * len(probs) * ws / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+           "d2h_bytes_per_step": d2h, "steps": e2e_steps}
+    xg = [x.clone() for x in xs]  # the grouped FP32 solutions of the last timed step
+    for G in probs:
+        G.close()
+    group.close()
+
+    # ---- each problem alone (ordinary handle, sequential), FP32 and FP64 plain
+    alone = {"fp32_ms": [], "fp32_outer_iterations": [], "bitwise_equal_to_grouped": []}
     fp64 = {"solves": 0, "ms": 0.0}
+    errs, its64 = [], []
     t_start = time.perf_counter()
-    errs, its64, its32 = [], [], []
-    x64 = torch.zeros(n, dtype=torch.float64, device="cuda")
-    for i, b in enumerate(W["betas"]):
-        if a.fp64_budget_s <= 0 or time.perf_counter() - t_start > a.fp64_budget_s:
-            break
-        G64, _ = make(b, 0, replica_seeds(rank, i + 1)[i])
-        x64.zero_()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        inf = G64.solve(x64)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        fp64["solves"] += 1
-        fp64["ms"] += e0.elapsed_time(e1)
-        its64.append(inf.outer_iterations)
-        x.zero_()
-        inf32 = probs[i][0].solve(x)
-        its32.append(inf32.outer_iterations)
-        errs.append(float(torch.linalg.norm(x - x64) / torch.linalg.norm(x64)))
-        G64.close()
+    x1 = torch.zeros(n, dtype=torch.float64, device="cuda")
+    st0 = torch.cuda.current_stream()
+    for k, b in enumerate(betas):
+        for prec in (1, 0):
+            if prec == 0 and (a.fp64_budget_s <= 0 or time.perf_counter() - t_start > a.fp64_budget_s):
+                continue
+            G = binding.Problem(params(b, prec), stream=st0.cuda_stream)
+            G.set_data(vds[k])
+            x1.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st0)
+            inf = G.solve(x1)
+            e1.record(st0)
+            torch.cuda.synchronize()
+            G.close()
+            if prec:
+                alone["fp32_ms"].append(round(e0.elapsed_time(e1), 1))
+                alone["fp32_outer_iterations"].append(inf.outer_iterations)
+                alone["bitwise_equal_to_grouped"].append(bool(torch.equal(x1, xg[k])))
+            else:
+                fp64["solves"] += 1
+                fp64["ms"] += e0.elapsed_time(e1)
+                its64.append(inf.outer_iterations)
+                errs.append(float(torch.linalg.norm(xg[k] - x1) / torch.linalg.norm(x1)))
     fp64_value = fp64["solves"] / (fp64["ms"] / 1e3) if fp64["solves"] else None
+    alone["value"] = round(len(alone["fp32_ms"]) / (sum(alone["fp32_ms"]) / 1e3), 4)
+    alone["note"] = "each problem solved alone on an ordinary handle, one after the other"
 
     # ---- roofline of the dominant kernel (multigrid on the velocity fields):
     # the library's algorithmic bytes of every launch (only the fields of
@@ -417,29 +486,39 @@ def run_ours(a):
     alg = mg["bytes"] / max(1, mg["launches"])
     achieved = mg["bytes"] / (mg["ms"] / 1e3) / 1e9 if mg["timed"] == mg["launches"] and mg["ms"] > 0 else None
     apply_line = apply_roofline(cls, hbm, src)
-    traffic = profiled_traffic("mg_q2b_kernel_stokes64_nt256.md", "k_mg.cu") if a.workload == "stokes64_nt256" \
-        else None
-
-    dft_line = dft_report(probs[0][0].sizes, dft, peaks_bf16(), W.get("dft_mode", 0))
+    traffic = None
+    if a.workload == "stokes64_nt256":
+        full = profiled_traffic("mg_q2p_kernel_stokes64_nt256.md", "k_mgp.cu")
+        if full:
+            # captured on a full launch (every field active): scaled to the average launch by its fields
+            sz = probs[0].sizes
+            traffic = int(full * alg / algorithmic_bytes_mg_q2(sz, 4 * sz.J, 4, 4))
+    dft_line = dft_report(probs[0].sizes, dft, peaks_bf16(), W.get("dft_mode", 0))
 
     line = {
         "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": ws, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": round(total_ms / a.steps, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32 preconditioner / f64 FGMRES",
         "data": "synthetic (seeded curl of 4 random sine modes)",
-        "config": workload_config(a.workload, ws),
+        "config": dict(workload_config(a.workload, ws),
+                       step=f"the {len(probs)} problems (one per beta) solved concurrently, one host thread and "
+                            "stream each, frequency solves shared in one group"),
         "latency_ms": {"p50": round(float(np.percentile(lat, 50)), 3), "p99": round(float(np.percentile(lat, 99)), 3)},
         "outer_iterations": [inf.outer_iterations for inf in infos],
         "relres": [inf.relres for inf in infos],
+        "shared": gstats,
+        "alone_fp32": alone,
         "fp64_plain": {"value": round(fp64_value, 5) if fp64_value else None, "unit": UNIT,
                        "solves": fp64["solves"], "outer_iterations": its64,
                        "speedup_fp32_over_fp64": round(value / fp64_value, 2) if fp64_value else None,
-                       "betas": W["betas"][:len(its64)], "fp32_outer_iterations": its32,
+                       "speedup_fp32_alone_over_fp64": round(alone["value"] / fp64_value, 2) if fp64_value else None,
+                       "betas": betas[:len(its64)], "fp32_outer_iterations": alone["fp32_outer_iterations"],
                        "fp32_vs_fp64_solution_relerr": errs},
         "e2e": e2e,
         "gpu_launches": int(launches),
         "kernel_time_share": shares,
-        "roofline": {"kernel": "mg_q2b_kernel<float> (multigrid W_j, 4 V-cycles, 4 fields x all frequencies)",
+        "roofline": {"kernel": "mg_q2p_kernel<float, 64> (multigrid W_j, 4 V-cycles, 4 fields x all active "
+                               "frequencies of the batch)",
                      "bound": "hbm", "achieved": round(achieved, 1) if achieved else None,
                      "peak": hbm, "peak_source": src, "unit": "GB/s",
                      "frac": round(achieved / hbm, 4) if achieved else None, "traffic": traffic,
@@ -454,8 +533,6 @@ def run_ours(a):
         line["cpu_baseline"] = cpu_baseline(W, a.cpu_sample_s, [inf.outer_iterations for inf in infos])
     if rank == 0:
         print(json.dumps(line), flush=True)
-    for G, _ in probs:
-        G.close()
     if dist:
         dist.destroy_process_group()
 

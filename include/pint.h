@@ -340,6 +340,48 @@ pint_status pint_profile_enable(pint_handle h, unsigned mask);
 pint_status pint_profile_read(pint_handle h, pint_profile* out);
 
 /* ------------------------------------------------------------------------
+ * Groups: shared frequency solves of several problems.
+ *
+ * Handles created in a group (pint_create_in_group) solve like any handle,
+ * but the frequency solves of their preconditioner applies (Algorithm 2 /
+ * the Uzawa variant over all frequencies of the Hermitian half) run batched
+ * with those of the group's other handles: problems that share grid level,
+ * domain, wind, nu, precision and the inner-solver settings (inner_tol,
+ * inner_maxit, fixed_inner_its, multigrid, Chebyshev and Uzawa counts,
+ * mu, sor_omega, sor_omega_conv, linear) form a subgroup whose members'
+ * applies, when several are pending, run as ONE set of launches over all
+ * their frequencies, each frequency with the constants of its own problem
+ * (tau, beta, n_t); a batch waits at most 3 ms for members that are inside
+ * pint_solve / pint_solve_host but still in their outer step.  Each handle
+ * keeps its outer FGMRES, KKT matvec and time DFT on its own stream.  The
+ * frequencies are independent (Sec. 3.1), so every result is bit for bit the
+ * one of the same problem solved on an ordinary handle.  Solves on handles
+ * of one group share launches only when they run concurrently (one host
+ * thread per solve).  No counterpart in the paper (its frequency blocks are
+ * distributed over processes, Sec. 5.3).  PINT_WIND_NODAL handles cannot
+ * join a group (PINT_ERR_ARG).  A group's shared workspace is allocated
+ * when a batch first needs it and grows with the largest batch; it is freed
+ * with the group's last handle.  Destroy every handle of a group before the
+ * group. */
+typedef struct pint_batcher_s* pint_group;
+typedef struct {
+  long long batches;       /* shared frequency solves run                        */
+  long long member_solves; /* preconditioner applies they served (sum of sizes)  */
+  long long frequencies;   /* frequencies solved in them                         */
+  int max_members;         /* most applies in one batch                          */
+} pint_group_stats;
+pint_status pint_group_create(pint_group* out);
+pint_status pint_create_in_group(pint_group g, const pint_params* p, void* stream, pint_handle* out);
+pint_status pint_group_get_stats(pint_group g, pint_group_stats* out);
+/* Tracing of a group's shared frequency solves, as pint_profile_enable /
+ * pint_profile_read for a handle: counters summed over all batches since the
+ * reset, class PINT_PROF_APPLY timing whole batches (the handles' own
+ * counters cover their outer solves and time DFTs). */
+pint_status pint_group_profile_enable(pint_group g, unsigned mask);
+pint_status pint_group_profile_read(pint_group g, pint_profile* out);
+pint_status pint_group_destroy(pint_group g);
+
+/* ------------------------------------------------------------------------
  * Serving loop: continuous batching of control problems.
  *
  * A server owns max_active worker slots on the current device.  Requests

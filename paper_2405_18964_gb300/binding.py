@@ -103,6 +103,12 @@ _SIGS = {
     "pint_autotune": (None, [ctypes.c_int]),
     "pint_autotune_report": (ctypes.c_size_t, [ctypes.c_char_p, ctypes.c_size_t]),
     "pint_server_create": (ctypes.c_int, [ctypes.POINTER(ServerParams), ctypes.POINTER(_P)]),
+    "pint_group_create": (ctypes.c_int, [ctypes.POINTER(_P)]),
+    "pint_create_in_group": (ctypes.c_int, [_P, ctypes.POINTER(Params), _P, ctypes.POINTER(_P)]),
+    "pint_group_get_stats": (ctypes.c_int, [_P, _P]),
+    "pint_group_destroy": (ctypes.c_int, [_P]),
+    "pint_group_profile_enable": (ctypes.c_int, [_P, ctypes.c_uint]),
+    "pint_group_profile_read": (ctypes.c_int, [_P, _P]),
     "pint_server_submit": (ctypes.c_int, [_P, ctypes.POINTER(Params), _P, _P, _P, ctypes.POINTER(ctypes.c_longlong)]),
     "pint_server_wait": (ctypes.c_int, [_P, ctypes.c_longlong, _P, ctypes.POINTER(SolveInfo),
                                         ctypes.POINTER(ctypes.c_double)]),
@@ -183,13 +189,16 @@ def default_params(**kw):
 class Problem:
     """One discrete control problem on the GPU (handle of the C ABI)."""
 
-    def __init__(self, params, stream=None, wind=None):
+    def __init__(self, params, stream=None, wind=None, group=None):
         """wind: for params.wind = PINT_WIND_NODAL (3), the wind's values at
-        the finest Q2 nodes, shape (2, (2N+1)^2)."""
+        the finest Q2 nodes, shape (2, (2N+1)^2).  group: a Group whose
+        handles share their frequency solves (pint_create_in_group)."""
         self.params = params
         h = ctypes.c_void_p()
         st = ctypes.c_void_p(stream) if stream else None
-        if wind is None:
+        if group is not None:
+            _check(lib().pint_create_in_group(group.h, ctypes.byref(params), st, ctypes.byref(h)))
+        elif wind is None:
             _check(lib().pint_create(ctypes.byref(params), st, ctypes.byref(h)))
         else:
             n2 = 2 * 2 ** params.level + 1
@@ -363,6 +372,44 @@ def autotune_report():
 def estimate_device_bytes(params):
     """Upper estimate of the device memory a handle for these parameters holds."""
     return int(lib().pint_estimate_device_bytes(ctypes.byref(params)))
+
+
+class GroupStats(ctypes.Structure):
+    _fields_ = [("batches", ctypes.c_longlong), ("member_solves", ctypes.c_longlong),
+                ("frequencies", ctypes.c_longlong), ("max_members", ctypes.c_int)]
+
+
+class Group:
+    """Handles whose frequency solves run in shared launches when they solve
+    concurrently (pint_group_*); close it after its handles."""
+
+    def __init__(self):
+        h = ctypes.c_void_p()
+        _check(lib().pint_group_create(ctypes.byref(h)))
+        self.h = h
+
+    def profile_enable(self, classes=()):
+        """Reset the shared solves' counters; time the named kernel classes."""
+        mask = 0
+        for c in classes:
+            mask |= 1 << PROF_CLASSES.index(c)
+        _check(lib().pint_group_profile_enable(self.h, mask))
+
+    def profile_read(self):
+        p = Profile()
+        _check(lib().pint_group_profile_read(self.h, ctypes.byref(p)))
+        return {c: {"launches": p.launches[i], "timed": p.timed[i], "ms": p.ms[i], "bytes": p.bytes[i]}
+                for i, c in enumerate(PROF_CLASSES)}
+
+    def stats(self):
+        st = GroupStats()
+        _check(lib().pint_group_get_stats(self.h, ctypes.byref(st)))
+        return {f: getattr(st, f) for f, _ in GroupStats._fields_}
+
+    def close(self):
+        if self.h:
+            lib().pint_group_destroy(self.h)
+            self.h = None
 
 
 class Server:

@@ -1477,8 +1477,13 @@ pint_status pint_convection_stencils(const pint_params* p, const double* wind_ho
   return PINT_OK;
 }
 
+void member_destroy(pint_handle h);
+
 pint_status pint_destroy(pint_handle h) {
-  free_ctx(h);
+  if (h && h->role == 1)
+    member_destroy(h);
+  else
+    free_ctx(h);
   return PINT_OK;
 }
 
@@ -1624,6 +1629,11 @@ pint_status pint_apply_preconditioner(pint_handle h, const double* r, double* z)
   return tc_status(h);
 }
 
+}  // extern "C"
+static void member_solve_begin(pint_handle h);
+static void member_solve_end(pint_handle h);
+extern "C" {
+
 pint_status pint_solve(pint_handle h, double* x, pint_solve_info* info) {
   if (!h || !x) {
     g_err = "null argument";
@@ -1634,7 +1644,9 @@ pint_status pint_solve(pint_handle h, double* x, pint_solve_info* info) {
   if (!h->cu(cudaMemcpyAsync(h->ox, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->st), "copy x0"))
     return PINT_ERR_CUDA;
   { PROF(h, PINT_PROF_OTHER, 1); launch_mask_blocks(h->s, h->K, 1, h->ox, h->st); }
+  if (h->role == 1) member_solve_begin(h);
   pint_status rc = fgmres(h, h->ox, info);
+  if (h->role == 1) member_solve_end(h);
   if (!h->cu(cudaMemcpyAsync(x, h->ox, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->st), "copy x") ||
       !h->cu(cudaStreamSynchronize(h->st), "solve"))
     return PINT_ERR_CUDA;
@@ -1652,7 +1664,9 @@ pint_status pint_solve_host(pint_handle h, double* x_host, pint_solve_info* info
   if (!h->cu(cudaMemcpyAsync(h->ox, x_host, sizeof(double) * n, cudaMemcpyHostToDevice, h->st), "upload x0"))
     return PINT_ERR_CUDA;
   { PROF(h, PINT_PROF_OTHER, 1); launch_mask_blocks(h->s, h->K, 1, h->ox, h->st); }
+  if (h->role == 1) member_solve_begin(h);
   pint_status rc = fgmres(h, h->ox, info);
+  if (h->role == 1) member_solve_end(h);
   if (!h->cu(cudaMemcpyAsync(x_host, h->ox, sizeof(double) * n, cudaMemcpyDeviceToHost, h->st), "download x") ||
       !h->cu(cudaStreamSynchronize(h->st), "solve"))
     return PINT_ERR_CUDA;
@@ -2074,7 +2088,11 @@ struct pint_batcher_s {
   std::condition_variable cv;
   std::map<std::string, BatchGroup*> groups;
   double window_ms = 3.0;  // how long a batch waits for members still in their outer step
-  pint_batch_stats stats{};
+  pint_group_stats stats{};
+  // profile of the shared contexts (summed over batches; class APPLY = whole batches)
+  std::mutex pmu;
+  unsigned prof_mask = 0;
+  pint_profile prof{};
 };
 
 namespace {
@@ -2136,10 +2154,17 @@ pint_status run_batch(BatchGroup* g, std::vector<BatchMember*>& batch) {
     off += bytes;
   }
   std::vector<int> its(jtot, 0);
-  if (b->fp32)
-    b->e32.freq_solve(b->e32.R, b->e32.Y, its.data());
-  else
-    b->e64.freq_solve(b->e64.R, b->e64.Y, its.data());
+  {
+    std::lock_guard<std::mutex> pk(g->owner->pmu);
+    b->prof_mask = g->owner->prof_mask;
+  }
+  {
+    PROF(b, PINT_PROF_APPLY, 0);
+    if (b->fp32)
+      b->e32.freq_solve(b->e32.R, b->e32.Y, its.data());
+    else
+      b->e64.freq_solve(b->e64.R, b->e64.Y, its.data());
+  }
   off = 0;
   int j0 = 0;
   for (BatchMember* m : batch) {
@@ -2152,6 +2177,21 @@ pint_status run_batch(BatchGroup* g, std::vector<BatchMember*>& batch) {
   }
   if (!b->launched("shared frequency solve") || !b->cu(cudaStreamSynchronize(b->st), "shared frequency solve"))
     return PINT_ERR_CUDA;
+  if (b->st_aux) cudaStreamSynchronize(b->st_aux);
+  b->drain();
+  {
+    // fold this batch's counters into the group's profile
+    std::lock_guard<std::mutex> pk(g->owner->pmu);
+    pint_profile& P = g->owner->prof;
+    for (int i = 0; i < PINT_PROF_CLASSES; ++i) {
+      P.launches[i] += b->prof_launch[i];
+      P.timed[i] += b->prof_timed[i];
+      P.ms[i] += b->prof_ms[i];
+      P.bytes[i] += b->prof_bytes[i];
+      b->prof_launch[i] = b->prof_timed[i] = 0;
+      b->prof_ms[i] = b->prof_bytes[i] = 0.0;
+    }
+  }
   return PINT_OK;
 }
 
@@ -2245,20 +2285,20 @@ void member_destroy(pint_handle h) {
   free_ctx(h);
 }
 
-void member_solve_begin(pint_handle h) {
+static void member_solve_begin(pint_handle h) {
   std::lock_guard<std::mutex> lk(h->group->owner->mu);
   h->group->in_solve++;
   h->in_solve = true;
 }
 
-void member_solve_end(pint_handle h) {
+static void member_solve_end(pint_handle h) {
   std::lock_guard<std::mutex> lk(h->group->owner->mu);
   h->group->in_solve--;
   h->in_solve = false;
   h->group->owner->cv.notify_all();
 }
 
-void batcher_get_stats(pint_batcher_s* B, pint_batch_stats* out) {
+void batcher_get_stats(pint_batcher_s* B, pint_group_stats* out) {
   std::lock_guard<std::mutex> lk(B->mu);
   *out = B->stats;
 }
@@ -2282,3 +2322,45 @@ void shared_estimates(const pint_params* p, size_t* member_bytes, size_t* per_fr
   f += std::max((long long)(oseen ? 2 : 0) * 2 * ns, 2LL * 2 * nq) * cs;
   *per_freq_bytes = (size_t)(f + f / 20);
 }
+
+extern "C" {
+
+pint_status pint_group_create(pint_group* out) {
+  if (!out) return g_err = "null argument", PINT_ERR_ARG;
+  *out = batcher_create();
+  return PINT_OK;
+}
+
+pint_status pint_create_in_group(pint_group g, const pint_params* p, void* stream, pint_handle* out) {
+  if (!g || !p || !out) return g_err = "null argument", PINT_ERR_ARG;
+  *out = nullptr;
+  return member_create(g, p, stream, out);
+}
+
+pint_status pint_group_get_stats(pint_group g, pint_group_stats* out) {
+  if (!g || !out) return g_err = "null argument", PINT_ERR_ARG;
+  batcher_get_stats(g, out);
+  return PINT_OK;
+}
+
+pint_status pint_group_profile_enable(pint_group g, unsigned mask) {
+  if (!g) return g_err = "null group", PINT_ERR_ARG;
+  std::lock_guard<std::mutex> pk(g->pmu);
+  g->prof_mask = mask;
+  g->prof = pint_profile{};
+  return PINT_OK;
+}
+
+pint_status pint_group_profile_read(pint_group g, pint_profile* out) {
+  if (!g || !out) return g_err = "null argument", PINT_ERR_ARG;
+  std::lock_guard<std::mutex> pk(g->pmu);
+  *out = g->prof;
+  return PINT_OK;
+}
+
+pint_status pint_group_destroy(pint_group g) {
+  batcher_destroy(g);
+  return PINT_OK;
+}
+
+}  // extern "C"

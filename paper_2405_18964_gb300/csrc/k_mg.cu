@@ -791,7 +791,8 @@ std::atomic<bool> g_tune_on{true};
 std::atomic<int> g_fixed_threads{0}, g_fixed_staging{-1};
 
 // Candidate for this launch; slot >= 0 means "time this launch into slot".
-// ncand: 3 (CTA sizes only) or 6 (also the shared-memory staging).
+// ncand: the first ncand of TUNE_CAND (2 or 3: CTA sizes only; 6: also the
+// shared-memory staging).
 TuneCand tune_pick(const MgKey& key, int ncand, TuneCand fallback, int& slot, cudaEvent_t& ea, cudaEvent_t& eb) {
   slot = -1;
   if (!g_tune_on.load()) return fallback;
@@ -895,8 +896,11 @@ void launch_mg(const MGLaunch<T>& Lin, cudaStream_t st) {
   } else if (tail) {
     pick = TuneCand{cta_threads(L.active_jobs), can_stage};
   } else {
-    pick = tune_pick(MgKey(L.space, L.lay.n[0], L.njobs, (int)sizeof(T), sized ? 3 : variant), can_stage ? 6 : 3,
-                     TuneCand{cta_threads(L.njobs), can_stage}, slot, ea, eb);
+    // (the compile-time-sized kernel's untuned default: 512 threads, its most frequent pick)
+    // (the compile-time-sized kernel runs at most 512 threads: candidates 256 and 512)
+    pick = tune_pick(MgKey(L.space, L.lay.n[0], L.njobs, (int)sizeof(T), sized ? 3 : variant),
+                     can_stage ? 6 : (sized ? 2 : 3), TuneCand{sized ? 512 : cta_threads(L.njobs), can_stage}, slot,
+                     ea, eb);
   }
   L.smem_levels = pick.smem ? plan : 0u;
   const size_t dyn = pick.smem ? sbytes : 0;

@@ -100,16 +100,11 @@ bool pint_server_s::run(Request* r, cudaStream_t st) {
   rc = pint_set_data(h, r->vd.data(), r->f.empty() ? nullptr : r->f.data(), r->v0.empty() ? nullptr : r->v0.data());
   if (rc == PINT_OK) {
     r->x.assign(r->kkt_len, 0.0);
-    if (batcher) member_solve_begin(h);
     rc = pint_solve_host(h, r->x.data(), &r->info);
-    if (batcher) member_solve_end(h);
   }
   if (rc != PINT_OK) r->msg = pint_last_error(h);
   r->status = rc;
-  if (batcher)
-    member_destroy(h);
-  else
-    pint_destroy(h);
+  pint_destroy(h);
   r->vd.clear();
   r->vd.shrink_to_fit();
   r->f.clear();
@@ -250,7 +245,7 @@ pint_status pint_server_get_stats(pint_server s, pint_server_stats* out) {
   out->bytes_in_use = s->in_use;
   out->bytes_peak = s->peak_bytes;
   out->active_peak = s->peak_active;
-  pint_batch_stats bs{};
+  pint_group_stats bs{};
   if (s->batcher) batcher_get_stats(s->batcher, &bs);
   out->shared_batches = bs.batches;
   out->shared_member_solves = bs.member_solves;
