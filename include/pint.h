@@ -446,24 +446,27 @@ const char* pint_server_last_error(void);
 
 /* Autotuner of the multigrid launches (on by default, process-wide): for
  * each launch shape (space, grid, number of fields, precision, operator
- * variant) six launches after the first three (untimed: module loading,
- * first touch of the workspaces) run with 256, 512 and 1024 threads per
- * CTA, twice each, timed by CUDA events on the launch stream; later
- * launches use the fastest on average.  For velocity fields the candidates
- * also include the shared-memory staging of the multigrid iterates (every
- * level whose iterate fits, finest first).  Results do not depend on the
- * choice.  pint_autotune(0) restores the fixed heuristic (1024 threads up to
- * one field per SM, 512 up to two, else 256; staging whenever it fits), or
- * the choice of pint_mg_launch_config. */
+ * variant) the launches after the first three (untimed: module loading,
+ * first touch of the workspaces) run each candidate twice, interleaved,
+ * timed by CUDA events on the launch stream; later launches use the fastest
+ * on average.  Candidates: 256 and 512 threads per CTA for the kernels with
+ * compile-time level sizes (velocity W_j, pressure operators), 256, 512 and
+ * 1024 threads for the general kernels, for the general velocity kernel
+ * each with and without the multigrid iterates staged in shared memory.
+ * Results do not depend on the choice.  pint_autotune(0) restores the fixed
+ * heuristic (1024 threads up to one field per SM, 512 up to two, else 256;
+ * the pressure kernel 512 up to one field per SM, else 256; staging
+ * whenever it fits), or the choice of pint_mg_launch_config. */
 void pint_autotune(int on);
 /* The multigrid launch choice used while the tuner is off (pint_autotune(0)),
- * process-wide: threads per CTA (256, 512, 1024; 0 = the fixed heuristic)
- * and the kernel variant for velocity fields: 1 or -1 = the fastest that
- * applies (the kernel with compile-time level sizes for the Stokes W_j on
- * grids of 4..256 elements per side, else the general kernel with the
- * iterates staged in shared memory where they fit), 0 = the general kernel
- * without staging.  Results agree to rounding; PINT_ERR_ARG for other
- * values. */
+ * process-wide: threads per CTA (256, 512, 1024; 0 = the fixed heuristic;
+ * the kernels with compile-time level sizes take at most 512) and the
+ * kernel variant: 1 or -1 = the kernels with compile-time level sizes where
+ * they apply (velocity W_j on grids of 4..256 elements per side, pressure
+ * operators on grids of 4..64), else the general kernels with the iterates
+ * staged in shared memory where they fit; 2 = the same with the general
+ * kernels unstaged; 0 = the general kernels only, unstaged.  Results agree
+ * bit for bit; PINT_ERR_ARG for other values. */
 pint_status pint_mg_launch_config(int threads, int staging);
 /* The tuner's decisions as text, one launch shape per line, written to buf
  * (NUL-terminated, truncated to len); returns the size needed. */

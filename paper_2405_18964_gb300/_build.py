@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build", "pint")
 LIB = os.path.join(HERE, "libpint.so")
-SOURCES = ["api.cu", "k_mg.cu", "k_mgp.cu", "k_fields.cu", "k_krylov.cu", "k_dft_tc.cu", "tables.cpp", "serve.cpp"]
+SOURCES = ["api.cu", "k_mg.cu", "k_mgp.cu", "k_mgq1.cu", "k_fields.cu", "k_krylov.cu", "k_dft_tc.cu", "tables.cpp", "serve.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]

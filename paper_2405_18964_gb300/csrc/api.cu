@@ -1852,8 +1852,8 @@ pint_status pint_mg_launch_config(int threads, int staging) {
     g_err = "threads must be 0, 256, 512 or 1024";
     return PINT_ERR_ARG;
   }
-  if (staging < -1 || staging > 1) {
-    g_err = "staging must be -1, 0 or 1";
+  if (staging < -1 || staging > 2) {
+    g_err = "staging must be -1, 0, 1 or 2";
     return PINT_ERR_ARG;
   }
   mg_fixed_config(threads, staging);

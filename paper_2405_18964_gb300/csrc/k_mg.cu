@@ -83,22 +83,6 @@ __device__ __forceinline__ cpx<T> stencil_q1d(const cpx<T>* __restrict__ w, T rs
   return acc;
 }
 
-// Row sums of a M on Q1 level l per node type (FP64 -> T): the mass part
-// only, the stiffness rows summing to zero.
-template <class T>
-__device__ void level_rowsums_q1(const Tabs<double>& t64, int l, int n, double a, T* srs) {
-  const double* tab = t64.q1[l];
-  for (int type = threadIdx.x; type < 9; type += blockDim.x) {
-    const int ix = type_rep<1>(type % 3, n), iy = type_rep<1>(type / 3, n);
-    double sx = 0.0, sy = 0.0;
-    for (int d = 0; d < 3; ++d) {
-      sx += tab[(size_t)ix * 3 + d];
-      sy += tab[(size_t)iy * 3 + d];
-    }
-    srs[type] = T(a * sx * sy);
-  }
-}
-
 template <int SP>
 __device__ __forceinline__ bool is_unknown(int ix, int iy, int n) {
   if (SP == 2) return ix > 0 && iy > 0 && ix < n - 1 && iy < n - 1;
@@ -787,7 +771,9 @@ std::mutex g_tune_mu;
 std::map<MgKey, MgTune> g_tune;
 std::atomic<bool> g_tune_on{true};
 // fixed choice used while the tuner is off: CTA threads (0 = by job count)
-// and staging (-1 = stage whenever the plan holds a level, 0 = never, 1 = always)
+// and staging (-1 or 1 = the compile-time-sized kernels where they apply,
+// else the general kernels staged; 2 = the same with the general kernels
+// unstaged; 0 = the general kernels only, unstaged)
 std::atomic<int> g_fixed_threads{0}, g_fixed_staging{-1};
 
 // Candidate for this launch; slot >= 0 means "time this launch into slot".
@@ -880,6 +866,9 @@ void launch_mg(const MGLaunch<T>& Lin, cudaStream_t st) {
   // (pint_mg_launch_config with staging 0 selects the general kernels)
   const bool sized = L.space == 2 && !L.conv && !L.cw && (L.lay.n[0] - 1) / 2 >= 4 &&
                      (L.lay.n[0] - 1) / 2 <= 256 && (g_tune_on.load() || g_fixed_staging.load() != 0);
+  // likewise for the real pressure operators
+  const bool sized1 = L.space == 1 && !L.conv && !L.cw && L.lay.n[0] - 1 >= 4 && L.lay.n[0] - 1 <= 64 &&
+                      (g_tune_on.load() || g_fixed_staging.load() != 0);
   // shared-memory staging plan of the velocity iterates (nothing for Q1)
   size_t sbytes = 0;
   const unsigned plan = L.space == 2 && !sized ? q2_smem_plan<T>(L.lay, q2_smem_budget<T>(), &sbytes) : 0u;
@@ -887,20 +876,27 @@ void launch_mg(const MGLaunch<T>& Lin, cudaStream_t st) {
   // When only some frequencies are still active (late inner iterations), the
   // few live fields get larger CTAs; otherwise the tuned choice for this shape.
   const bool tail = L.active_jobs > 0 && L.active_jobs < L.njobs;
+  // untuned CTA size: by job count; the pressure kernel runs 512 threads up
+  // to one field per SM, else 256 (two CTAs per SM)
+  auto def_threads = [&](int jobs) {
+    const int t = cta_threads(jobs);
+    return sized1 ? (t >= 1024 ? 512 : 256) : t;
+  };
   TuneCand pick;
   if (L.no_tune) {
-    pick = TuneCand{cta_threads(L.njobs), can_stage};
+    pick = TuneCand{def_threads(L.njobs), can_stage};
   } else if (!g_tune_on.load()) {
     const int ft = g_fixed_threads.load(), fs = g_fixed_staging.load();
-    pick = TuneCand{ft > 0 ? ft : cta_threads(tail ? L.active_jobs : L.njobs), can_stage && fs != 0};
+    pick = TuneCand{ft > 0 ? ft : def_threads(tail ? L.active_jobs : L.njobs), can_stage && fs != 0 && fs != 2};
   } else if (tail) {
-    pick = TuneCand{cta_threads(L.active_jobs), can_stage};
+    pick = TuneCand{def_threads(L.active_jobs), can_stage};
   } else {
-    // (the compile-time-sized kernel's untuned default: 512 threads, its most frequent pick)
-    // (the compile-time-sized kernel runs at most 512 threads: candidates 256 and 512)
-    pick = tune_pick(MgKey(L.space, L.lay.n[0], L.njobs, (int)sizeof(T), sized ? 3 : variant),
-                     can_stage ? 6 : (sized ? 2 : 3), TuneCand{sized ? 512 : cta_threads(L.njobs), can_stage}, slot,
-                     ea, eb);
+    // (the compile-time-sized kernels run at most 512 threads: candidates 256
+    // and 512; untuned defaults 512 for the velocity kernel, 256 for the
+    // pressure kernel, their most frequent picks)
+    pick = tune_pick(MgKey(L.space, L.lay.n[0], L.njobs, (int)sizeof(T), sized ? 3 : (sized1 ? 4 : variant)),
+                     can_stage ? 6 : (sized || sized1 ? 2 : 3),
+                     TuneCand{sized ? 512 : (sized1 ? 256 : cta_threads(L.njobs)), can_stage}, slot, ea, eb);
   }
   L.smem_levels = pick.smem ? plan : 0u;
   const size_t dyn = pick.smem ? sbytes : 0;
@@ -908,6 +904,8 @@ void launch_mg(const MGLaunch<T>& Lin, cudaStream_t st) {
   if (slot >= 0) cudaEventRecord(ea, st);
   if (sized && launch_mg_q2p<T>(L, pick.threads, st)) {
     // launched by the compile-time-sized kernel
+  } else if (sized1 && launch_mg_q1p<T>(L, pick.threads, st)) {
+    // launched by the compile-time-sized pressure kernel
   } else if (L.space == 2) {
     // one velocity field per CTA, class-blocked layout in the workspace
     if (L.conv)

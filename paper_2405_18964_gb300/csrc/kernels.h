@@ -78,6 +78,10 @@ __host__ __device__ constexpr int q2p_pitch(int N) {
 // covers; false (nothing launched) for the others.
 template <class T>
 bool launch_mg_q2p(const MGLaunch<T>& L, int threads, cudaStream_t st);
+// The compile-time-sized pressure multigrid (k_mgq1.cu) for the launches it
+// covers; false (nothing launched) for the others.
+template <class T>
+bool launch_mg_q1p(const MGLaunch<T>& L, int threads, cudaStream_t st);
 // CTA-size autotuner of launch_mg (on by default) and its decisions as text.
 void mg_autotune_enable(bool on);
 // Fixed launch choice while the tuner is off (threads 0 = by job count;

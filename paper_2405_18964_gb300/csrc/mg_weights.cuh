@@ -32,29 +32,54 @@ __device__ __forceinline__ int node_type(int ix, int iy, int n) {
   return tx + 3 * ty;
 }
 
+// Entry q = type * (stencil size) + k of level_weights: sw[q] = (a M + b K)
+// at level l (FP64 -> T); sdi[type] = 1 / diagonal with the centre entry.
+template <class T, int SP>
+__device__ __forceinline__ void level_weight(const Tabs<double>& t64, int l, int n, cpx<double> a, double b, int q,
+                                             cpx<T>* sw, cpx<T>* sdi) {
+  constexpr int W = SP == 2 ? 5 : 3;
+  const double* tab = SP == 2 ? t64.q2[l] : t64.q1[l];
+  const int ns = nstencil<SP>();
+  const int type = q / ns, k = q % ns;
+  const int dx = k % W, dy = k / W;
+  const int tx = SP == 2 ? (type & 1) : type % 3;
+  const int ty = SP == 2 ? (type >> 1) : type / 3;
+  const int ix = type_rep<SP>(tx, n), iy = type_rep<SP>(ty, n);
+  const double mx = tab[(size_t)(0 * n + ix) * W + dx], my = tab[(size_t)(0 * n + iy) * W + dy];
+  const double kx = tab[(size_t)(1 * n + ix) * W + dx], ky = tab[(size_t)(1 * n + iy) * W + dy];
+  const double m2 = mx * my, k2 = kx * my + mx * ky;
+  const cpx<double> w = mkc<double>(a.x * m2 + b * k2, a.y * m2);
+  sw[q] = mkc<T>(T(w.x), T(w.y));
+  if (k == ns / 2) {
+    const double den = w.x * w.x + w.y * w.y;
+    sdi[type] = mkc<T>(T(w.x / den), T(-w.y / den));
+  }
+}
+
 // sw[type][k] = a M + b K at level l (FP64 -> T), sdi[type] = 1 / diagonal.
 template <class T, int SP>
 __device__ void level_weights(const Tabs<double>& t64, int l, int n, cpx<double> a, double b, cpx<T>* sw,
                               cpx<T>* sdi) {
-  constexpr int W = SP == 2 ? 5 : 3;
-  const double* tab = SP == 2 ? t64.q2[l] : t64.q1[l];
   const int nt = ntypes<SP>(), ns = nstencil<SP>();
-  for (int q = threadIdx.x; q < nt * ns; q += blockDim.x) {
-    const int type = q / ns, k = q % ns;
-    const int dx = k % W, dy = k / W;
-    const int tx = SP == 2 ? (type & 1) : type % 3;
-    const int ty = SP == 2 ? (type >> 1) : type / 3;
-    const int ix = type_rep<SP>(tx, n), iy = type_rep<SP>(ty, n);
-    const double mx = tab[(size_t)(0 * n + ix) * W + dx], my = tab[(size_t)(0 * n + iy) * W + dy];
-    const double kx = tab[(size_t)(1 * n + ix) * W + dx], ky = tab[(size_t)(1 * n + iy) * W + dy];
-    const double m2 = mx * my, k2 = kx * my + mx * ky;
-    const cpx<double> w = mkc<double>(a.x * m2 + b * k2, a.y * m2);
-    sw[q] = mkc<T>(T(w.x), T(w.y));
-    if (k == ns / 2) {
-      const double den = w.x * w.x + w.y * w.y;
-      sdi[type] = mkc<T>(T(w.x / den), T(-w.y / den));
-    }
+  for (int q = threadIdx.x; q < nt * ns; q += blockDim.x) level_weight<T, SP>(t64, l, n, a, b, q, sw, sdi);
+}
+
+// Row sum of a M on Q1 level l for one node type (FP64 -> T): the mass part
+// only, the stiffness rows summing to zero.
+template <class T>
+__device__ __forceinline__ T level_rowsum_q1(const Tabs<double>& t64, int l, int n, double a, int type) {
+  const double* tab = t64.q1[l];
+  const int ix = type_rep<1>(type % 3, n), iy = type_rep<1>(type / 3, n);
+  double sx = 0.0, sy = 0.0;
+  for (int d = 0; d < 3; ++d) {
+    sx += tab[(size_t)ix * 3 + d];
+    sy += tab[(size_t)iy * 3 + d];
   }
+  return T(a * sx * sy);
+}
+template <class T>
+__device__ void level_rowsums_q1(const Tabs<double>& t64, int l, int n, double a, T* srs) {
+  for (int type = threadIdx.x; type < 9; type += blockDim.x) srs[type] = level_rowsum_q1<T>(t64, l, n, a, type);
 }
 
 }  // namespace pint
