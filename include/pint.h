@@ -449,9 +449,9 @@ const char* pint_server_last_error(void);
  * variant) the launches after the first three (untimed: module loading,
  * first touch of the workspaces) run each candidate twice, interleaved,
  * timed by CUDA events on the launch stream; later launches use the fastest
- * on average.  Candidates: 256 and 512 threads per CTA for the kernels with
- * compile-time level sizes (velocity W_j, pressure operators), 256, 512 and
- * 1024 threads for the general kernels, for the general velocity kernel
+ * on average.  Candidates: 256 and 512 threads per CTA for the kernels
+ * with compile-time level sizes (velocity W_j, pressure operators), 256,
+ * 512 and 1024 for the general kernels, for the general velocity kernel
  * each with and without the multigrid iterates staged in shared memory.
  * Results do not depend on the choice.  pint_autotune(0) restores the fixed
  * heuristic (1024 threads up to one field per SM, 512 up to two, else 256;

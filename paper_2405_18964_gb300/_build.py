@@ -15,7 +15,9 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build", "pint")
 LIB = os.path.join(HERE, "libpint.so")
-SOURCES = ["api.cu", "k_mg.cu", "k_mgp.cu", "k_mgq1.cu", "k_fields.cu", "k_krylov.cu", "k_dft_tc.cu", "tables.cpp", "serve.cpp"]
+SOURCES = ["api.cu", "k_mg.cu", "k_mgp.cu", "k_mgp64.cu", "k_mgq1.cu", "k_fields.cu", "k_krylov.cu", "k_dft_tc.cu", "tables.cpp", "serve.cpp"]
+# translation units that include another source file (one instantiation each)
+INCLUDED_SOURCES = {"k_mgp64.cu": ["k_mgp.cu"]}
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]
@@ -52,8 +54,9 @@ def build(force=False, verbose=False, extra_flags=()):
     for src in SOURCES:
         obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
         objs.append(obj)
+        deps = [os.path.join(CSRC, d) for d in [src] + INCLUDED_SOURCES.get(src, [])]
         stale = force or not os.path.exists(obj) or \
-            os.path.getmtime(obj) < max(os.path.getmtime(os.path.join(CSRC, src)), hdr)
+            os.path.getmtime(obj) < max([os.path.getmtime(d) for d in deps] + [hdr])
         if stale:
             todo.append((src, obj))
     if extra_flags:

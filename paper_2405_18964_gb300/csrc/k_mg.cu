@@ -876,11 +876,12 @@ void launch_mg(const MGLaunch<T>& Lin, cudaStream_t st) {
   // When only some frequencies are still active (late inner iterations), the
   // few live fields get larger CTAs; otherwise the tuned choice for this shape.
   const bool tail = L.active_jobs > 0 && L.active_jobs < L.njobs;
-  // untuned CTA size: by job count; the pressure kernel runs 512 threads up
-  // to one field per SM, else 256 (two CTAs per SM)
+  // untuned CTA size: by job count for the general kernels; the velocity
+  // kernel with compile-time level sizes 512; the pressure kernel 512 up to
+  // one field per SM, else 256 (two CTAs per SM)
   auto def_threads = [&](int jobs) {
     const int t = cta_threads(jobs);
-    return sized1 ? (t >= 1024 ? 512 : 256) : t;
+    return sized1 ? (t >= 1024 ? 512 : 256) : (sized ? 512 : t);
   };
   TuneCand pick;
   if (L.no_tune) {
@@ -891,9 +892,9 @@ void launch_mg(const MGLaunch<T>& Lin, cudaStream_t st) {
   } else if (tail) {
     pick = TuneCand{def_threads(L.active_jobs), can_stage};
   } else {
-    // (the compile-time-sized kernels run at most 512 threads: candidates 256
-    // and 512; untuned defaults 512 for the velocity kernel, 256 for the
-    // pressure kernel, their most frequent picks)
+    // (the kernels with compile-time level sizes run at most 512 threads:
+    // candidates 256 and 512; untuned defaults 512 for the velocity kernel,
+    // 256 for the pressure kernel)
     pick = tune_pick(MgKey(L.space, L.lay.n[0], L.njobs, (int)sizeof(T), sized ? 3 : (sized1 ? 4 : variant)),
                      can_stage ? 6 : (sized || sized1 ? 2 : 3),
                      TuneCand{sized ? 512 : (sized1 ? 256 : cta_threads(L.njobs)), can_stage}, slot, ea, eb);

@@ -131,16 +131,18 @@ struct Ctx {
   const double* inv;
 };
 
-// Warp groups: node types with 25, 15, 15 and 9 couplings get 3/8, 1/4, 1/4
-// and 1/8 of the CTA's warps.
+// Warp groups: a quarter of the CTA's warps per node type.  A colour phase
+// holds the same number of nodes of each type, and a thread's nodes are
+// processed one after another, each waiting for its right-hand side from L2
+// when that level's is not staged; equal groups give every group the same
+// number of such rounds (groups sized by coupling count, 3/8, 1/4, 1/4, 1/8,
+// left the 9-coupling nodes' group with twice the rounds of the others).
 __device__ __forceinline__ void type_group(int& g, int& t, int& nt) {
   const int W = blockDim.x >> 5, w = threadIdx.x >> 5;
-  const int b1 = 3 * W / 8, b2 = 5 * W / 8, b3 = 7 * W / 8;
-  const int lo = w < b1 ? 0 : (w < b2 ? b1 : (w < b3 ? b2 : b3));
-  const int hi = w < b1 ? b1 : (w < b2 ? b2 : (w < b3 ? b3 : W));
-  g = w < b1 ? 0 : (w < b2 ? 1 : (w < b3 ? 2 : 3));
-  t = threadIdx.x - 32 * lo;
-  nt = 32 * (hi - lo);
+  const int per = W >> 2;
+  g = w / per;
+  t = threadIdx.x - 32 * per * g;
+  nt = 32 * per;
 }
 
 // ---- level pointers: shared memory where the plan keeps the iterate -------
@@ -418,13 +420,11 @@ __device__ void vcycle(const Ctx<T, NF>& c, unsigned char* dsm) {
   }
 }
 
-// CTAs of up to 512 threads: 128 registers, enough to keep every tap of a
-// node's stencil in flight (with 64 the loads and FMAs serialise)
-template <class T>
-constexpr int mgp_max_threads() { return 512; }
-
+// CTAs of up to 512 threads, one per SM: 128 registers a thread (measured
+// at 64 x 64 elements: 2.52 ms per 516-field launch at 512 threads against
+// 2.83 ms for a 1024-thread variant with 64 registers)
 template <class T, int NF>
-__global__ void __launch_bounds__(mgp_max_threads<T>(), 1) mg_q2p_kernel(MGLaunch<T> L) {
+__global__ void __launch_bounds__(512, 1) mg_q2p_kernel(MGLaunch<T> L) {
   constexpr int NL = ilog2c(NF);
   using V0 = PLev<NF, 0>;
   constexpr int n0 = 2 * NF + 1;
@@ -499,7 +499,7 @@ bool launch_nf(const MGLaunch<T>& L, int threads, cudaStream_t st) {
     return e == cudaSuccess;
   }();
   if (!ok) return false;
-  mg_q2p_kernel<T, NF><<<L.njobs, threads, (size_t)PL::BYTES, st>>>(L);
+  mg_q2p_kernel<T, NF><<<L.njobs, threads > 512 ? 512 : threads, (size_t)PL::BYTES, st>>>(L);
   return true;
 }
 
@@ -507,13 +507,12 @@ bool launch_nf(const MGLaunch<T>& L, int threads, cudaStream_t st) {
 
 // Launches the compile-time-sized velocity multigrid when it covers this
 // launch (real operator W_j, no convection, finest grid of 4..256 elements
-// per side, one field per job, a multiple of 128 threads: at most 1024 in
-// FP32, 512 in FP64, larger requests are reduced); returns false (nothing
-// launched) otherwise.
+// per side, one field per job, 128..1024 threads in multiples of 128, more
+// than 512 run as 512); returns false (nothing launched) otherwise.
 template <class T>
 bool launch_mg_q2p(const MGLaunch<T>& L, int threads, cudaStream_t st) {
-  if (L.space != 2 || L.conv || L.cw || threads < 128 || threads % 128) return false;
-  threads = threads > mgp_max_threads<T>() ? mgp_max_threads<T>() : threads;
+  if (L.space != 2 || L.conv || L.cw || L.fields_per_job != 1 || threads < 128 || threads % 128 || threads > 1024)
+    return false;
   const int N = (L.lay.n[0] - 1) / 2;
   if (L.lay.nlev != ilog2c(N) || (1 << L.lay.nlev) != N) return false;
   switch (N) {
@@ -528,7 +527,12 @@ bool launch_mg_q2p(const MGLaunch<T>& L, int threads, cudaStream_t st) {
   }
 }
 
+// FP32 here, FP64 in k_mgp64.cu (a translation unit of its own, so that the
+// build compiles the two in parallel)
+#ifndef PINT_MGP_FP64
 template bool launch_mg_q2p<float>(const MGLaunch<float>&, int, cudaStream_t);
+#else
 template bool launch_mg_q2p<double>(const MGLaunch<double>&, int, cudaStream_t);
+#endif
 
 }  // namespace pint

@@ -43,8 +43,7 @@ template <int NF, int L>
 struct QLev {
   static constexpr int N = NF >> L;      // elements per side
   static constexpr int P = N / 2 + 2;    // row pitch of a colour sub-grid
-  static constexpr int SUB = P * P;      // one colour
-  static constexpr int SIZE = 4 * SUB;   // one level
+  static constexpr int SUB = P * P;      // one colour (a level: 4 SUB = qsize(N))
 };
 
 // shared-memory map (complex elements): iterates of levels 0..NL-1, right-
@@ -356,7 +355,7 @@ __global__ void __launch_bounds__(MAXT, MAXT <= 256 ? 2 : 1) mg_q1p_kernel(MGLau
   for (int q = threadIdx.x; q < q_roff<NF>(); q += blockDim.x) c.dsm[q] = czero<T>();
   {
     const cpx<T>* in = L.bbase + jb.b_off[0];
-    for (int q = threadIdx.x; q < V0::SIZE; q += blockDim.x) {
+    for (int q = threadIdx.x; q < qsize(NF); q += blockDim.x) {
       const int col = q / V0::SUB, rem = q - col * V0::SUB;
       const int ix = 2 * (rem % V0::P - 1) + (col & 1), iy = 2 * (rem / V0::P - 1) + (col >> 1);
       cpx<T> v = czero<T>();
@@ -380,7 +379,7 @@ bool q1_launch(const MGLaunch<T>& L, int threads, cudaStream_t st) {
   if constexpr (bytes > Q1P_SMEM_BUDGET) {
     return false;
   } else {
-    if (L.lay.per_job < QLev<NF, 0>::SIZE) return false;  // workspace too small for the residual
+    if (L.lay.per_job < qsize(NF)) return false;  // workspace too small for the residual
     static const bool ok = [] {
       const cudaError_t e =
           cudaFuncSetAttribute(mg_q1p_kernel<T, NF, MAXT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
