@@ -406,9 +406,27 @@ def run_ours(a):
         G.profile_enable(binding.PROF_CLASSES)
     step()
     g2 = group.profile_read()
-    share = {c: g2[c]["ms"] + sum(G.profile_read()[c]["ms"] for G in probs) for c in binding.PROF_CLASSES}
-    share_launch = {c: g2[c]["launches"] + sum(G.profile_read()[c]["launches"] for G in probs)
-                    for c in binding.PROF_CLASSES}
+    m2 = [G.profile_read() for G in probs]
+    share = {c: g2[c]["ms"] + sum(p[c]["ms"] for p in m2) for c in binding.PROF_CLASSES}
+    share_launch = {c: g2[c]["launches"] + sum(p[c]["launches"] for p in m2) for c in binding.PROF_CLASSES}
+    share_bytes = {c: g2[c]["bytes"] + sum(p[c]["bytes"] for p in m2) for c in binding.PROF_CLASSES}
+    hbm_p, src_p = peaks()
+    # per-class algorithmic bytes over the class's summed event time in this
+    # profiled step (every launch timed)
+    class_roofline = {}
+    for c in ("mg_q2", "mg_q1", "cheb", "block_mv", "combo", "inner", "kkt_mv", "outer"):
+        if share[c] > 0 and share_bytes[c] > 0:
+            gbs = share_bytes[c] / (share[c] / 1e3) / 1e9
+            class_roofline[c] = {"GBps": round(gbs, 1), "frac": round(gbs / hbm_p, 4), "launches": int(share_launch[c])}
+    class_roofline["peak"] = hbm_p
+    class_roofline["peak_source"] = src_p
+    class_roofline["note"] = ("event times of launches that share the GPU with the other stream: the pressure part "
+                              "(mg_q1, cheb) runs beside the velocity multigrid and its launches wait for SMs held "
+                              "by it, so their fractions are lower bounds; serialised times are in profiles/")
+    inner_loop = {"host_syncs_per_solve": round((g2["host_syncs"] + sum(p["host_syncs"] for p in m2)) / len(probs), 1),
+                  "gpu_launches_per_solve": round(sum(share_launch.values()) / len(probs), 1),
+                  "note": "one host synchronisation per inner GMRES step of a shared batch (the host reads how many "
+                          "frequencies are still active), two per outer FGMRES step of each problem"}
     tot = sum(v for k, v in share.items() if k != "apply") or 1.0
     shares = {k: round(v / tot, 4) for k, v in share.items() if share_launch[k] and k != "apply"}
     shares["note"] = ("shares of the summed per-launch event times of one profiled step; the pressure part "
@@ -517,6 +535,8 @@ def run_ours(a):
         "e2e": e2e,
         "gpu_launches": int(launches),
         "kernel_time_share": shares,
+        "class_roofline": class_roofline,
+        "inner_loop": inner_loop,
         "roofline": {"kernel": "mg_q2p_kernel<float, 64> (multigrid W_j, 4 V-cycles, 4 fields x all active "
                                "frequencies of the batch)",
                      "bound": "hbm", "achieved": round(achieved, 1) if achieved else None,

@@ -332,6 +332,10 @@ typedef struct {
    * operator combinations their fields read and written once; only the
    * frequencies still active in the inner GMRES are counted. */
   double bytes[PINT_PROF_CLASSES];
+  /* Host synchronisations of the solve path since the reset: one per inner
+   * GMRES step (the host reads how many frequencies are still active), two
+   * per outer FGMRES step, one per shared batch of a group. */
+  long long host_syncs;
 } pint_profile;
 
 /* Reset the counters and select the timed classes (bit i = class i). */

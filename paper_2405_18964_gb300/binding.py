@@ -58,7 +58,15 @@ APPLY_CLASSES = ["mg_q2", "mg_q1", "cheb", "dft_fwd", "dft_inv", "block_mv", "co
 
 class Profile(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_longlong * 12), ("timed", ctypes.c_longlong * 12),
-                ("ms", ctypes.c_double * 12), ("bytes", ctypes.c_double * 12)]
+                ("ms", ctypes.c_double * 12), ("bytes", ctypes.c_double * 12), ("host_syncs", ctypes.c_longlong)]
+
+
+def _profile_dict(p):
+    """Per-class counters, plus the host synchronisations under "host_syncs"."""
+    out = {c: {"launches": p.launches[i], "timed": p.timed[i], "ms": p.ms[i], "bytes": p.bytes[i]}
+           for i, c in enumerate(PROF_CLASSES)}
+    out["host_syncs"] = p.host_syncs
+    return out
 
 
 _lib = None
@@ -317,8 +325,7 @@ class Problem:
     def profile_read(self):
         p = Profile()
         _check(lib().pint_profile_read(self.h, ctypes.byref(p)), self.h)
-        return {c: {"launches": p.launches[i], "timed": p.timed[i], "ms": p.ms[i], "bytes": p.bytes[i]}
-                for i, c in enumerate(PROF_CLASSES)}
+        return _profile_dict(p)
 
     def component_apply(self, which, j, x, y):
         w = COMPONENT[which] if isinstance(which, str) else int(which)
@@ -398,8 +405,7 @@ class Group:
     def profile_read(self):
         p = Profile()
         _check(lib().pint_group_profile_read(self.h, ctypes.byref(p)))
-        return {c: {"launches": p.launches[i], "timed": p.timed[i], "ms": p.ms[i], "bytes": p.bytes[i]}
-                for i, c in enumerate(PROF_CLASSES)}
+        return _profile_dict(p)
 
     def stats(self):
         st = GroupStats()

@@ -156,6 +156,7 @@ struct pint_ctx {
   // ---- tracing: launch counts per kernel class, event timing for masked classes
   unsigned prof_mask = 0;
   long long prof_launch[PINT_PROF_CLASSES] = {};
+  long long prof_syncs = 0;  // host synchronisations of the solve path (pint_profile.host_syncs)
   long long prof_timed[PINT_PROF_CLASSES] = {};
   double prof_ms[PINT_PROF_CLASSES] = {};
   double prof_bytes[PINT_PROF_CLASSES] = {};  // algorithmic bytes (pint.h, pint_profile)
@@ -550,6 +551,7 @@ void Engine<T>::inner_solve(const cpx<T>* S, cpx<T>* X, int* its_host) {
     launch_gmres_givens(G, i, c->p.inner_tol, c->p.fixed_inner_its, st);
     cudaMemcpyAsync(c->h_count, G.count, sizeof(int), cudaMemcpyDeviceToHost, st);
     cudaStreamSynchronize(st);
+    ++c->prof_syncs;
     c->drain();
     if (*c->h_count == 0) break;
   }
@@ -1235,6 +1237,7 @@ pint_status fgmres(pint_ctx* c, double* x, pint_solve_info* info) {
       auto a0 = now();
       apply_prec(c, Vi, Zi, its.data());
       cudaStreamSynchronize(st);
+      ++c->prof_syncs;
       if (c->batch_rc != PINT_OK) {
         inf.outer_iterations = total;
         if (info) *info = inf;
@@ -1261,6 +1264,7 @@ pint_status fgmres(pint_ctx* c, double* x, pint_solve_info* info) {
       }
       cudaMemcpyAsync(c->h_pinned, c->oh, sizeof(double) * (2 * (i + 1) + 1), cudaMemcpyDeviceToHost, st);
       if (!c->cu(cudaStreamSynchronize(st), "FGMRES iteration")) return PINT_ERR_CUDA;
+      ++c->prof_syncs;
       c->drain();
       for (int l = 0; l <= 2 * (i + 1); ++l)
         if (!std::isfinite(c->h_pinned[l])) {
@@ -1888,6 +1892,7 @@ pint_status pint_profile_enable(pint_handle h, unsigned mask) {
     h->prof_ms[i] = 0.0;
     h->prof_bytes[i] = 0.0;
   }
+  h->prof_syncs = 0;
   return PINT_OK;
 }
 
@@ -1901,6 +1906,7 @@ pint_status pint_profile_read(pint_handle h, pint_profile* out) {
     out->ms[i] = h->prof_ms[i];
     out->bytes[i] = h->prof_bytes[i];
   }
+  out->host_syncs = h->prof_syncs;
   return PINT_OK;
 }
 
@@ -2177,6 +2183,7 @@ pint_status run_batch(BatchGroup* g, std::vector<BatchMember*>& batch) {
   }
   if (!b->launched("shared frequency solve") || !b->cu(cudaStreamSynchronize(b->st), "shared frequency solve"))
     return PINT_ERR_CUDA;
+  ++b->prof_syncs;
   if (b->st_aux) cudaStreamSynchronize(b->st_aux);
   b->drain();
   {
@@ -2191,6 +2198,8 @@ pint_status run_batch(BatchGroup* g, std::vector<BatchMember*>& batch) {
       b->prof_launch[i] = b->prof_timed[i] = 0;
       b->prof_ms[i] = b->prof_bytes[i] = 0.0;
     }
+    P.host_syncs += b->prof_syncs;
+    b->prof_syncs = 0;
   }
   return PINT_OK;
 }

@@ -127,6 +127,8 @@ def test_group_shares_launches_and_profiles_them():
     assert st["batches"] == prof["apply"]["timed"]          # one timed scope per shared solve
     assert prof["mg_q2"]["launches"] >= prof["mg_q2"]["timed"] > 0
     assert prof["mg_q2"]["bytes"] > 0 and prof["mg_q2"]["ms"] > 0
+    # at least one host synchronisation per shared batch (plus one per inner step)
+    assert prof["host_syncs"] >= 2 * st["batches"]
 
 
 def test_nodal_wind_cannot_join_a_group():
