@@ -537,8 +537,10 @@ def run_ours(a):
         "kernel_time_share": shares,
         "class_roofline": class_roofline,
         "inner_loop": inner_loop,
-        "roofline": {"kernel": "mg_q2p_kernel<float, 64> (multigrid W_j, 4 V-cycles, 4 fields x all active "
-                               "frequencies of the batch)",
+        "roofline": {"kernel": (f"mg_q2p_kernel<float, {N}> (multigrid W_j, 4 V-cycles, 4 fields x all active "
+                                "frequencies of the batch)" if W["kind"] == 0 else
+                                "mg_q2b_kernel<float, conv> (multigrids of Q_j and Q_j^H, 4 V-cycles, 2 fields each "
+                                "x all active frequencies of the batch)"),
                      "bound": "hbm", "achieved": round(achieved, 1) if achieved else None,
                      "peak": hbm, "peak_source": src, "unit": "GB/s",
                      "frac": round(achieved / hbm, 4) if achieved else None, "traffic": traffic,
@@ -561,7 +563,7 @@ def run_ours(a):
 def serve_requests(seed, count, max_level):
     """The serving stream's requests, drawn from default_rng(seed) in this
     order per request: kind 50/50; N in {16, 32, 64, 128} (levels 4..7, capped
-    at max_level; Oseen requests drawn at 16x16 run at 32x32); n_t in
+    at max_level); n_t in
     {16, 32, 64, 128, 256}; log10 beta ~ U[-6, -2]; nu in {1/50, 1/100} for
     Oseen (1e-2 for Stokes); a data seed.  Oseen requests with beta > 1e-4
     damp the SOR of their convection multigrids (sor_omega_conv = 0.5: with
@@ -578,8 +580,6 @@ def serve_requests(seed, count, max_level):
         dseed = int(rng.integers(0, 2 ** 31))
         omega_conv = 0.0
         if oseen:
-            # 16x16 Oseen: the Uzawa/commutator inner solver stagnates (inner GMRES at its cap)
-            level = max(level, 5)
             omega_conv = 0.5 if beta > 1e-4 else 0.0
         out.append(dict(oseen=oseen, level=min(level, max_level), K=K, beta=beta, nu=nu, seed=dseed,
                         omega_conv=omega_conv))

@@ -19,11 +19,12 @@ def test_serving_requests_are_seeded_and_follow_the_recipe():
         assert 4 <= r["level"] <= 7
         assert 1e-6 <= r["beta"] <= 1e-2
         if r["oseen"]:
-            assert r["level"] >= 5 and r["nu"] in (1 / 50, 1 / 100)
+            assert r["nu"] in (1 / 50, 1 / 100)
             assert r["omega_conv"] == (0.5 if r["beta"] > 1e-4 else 0.0)
         else:
             assert r["nu"] == 1e-2 and r["omega_conv"] == 0.0
     assert any(r["oseen"] and r["beta"] > 1e-3 for r in a)  # the full beta range, Oseen included
+    assert any(r["oseen"] and r["level"] == 4 for r in a)   # and the full grid range
     kinds = [r["oseen"] for r in a]
     assert 16 < sum(kinds) < 48                           # 50/50 draw
     assert all(r["level"] <= 5 for r in bench.serve_requests(0, 64, 5))
