@@ -12,6 +12,12 @@ as explicit matrix iterations (dense, tiny grids).
   the nested interpolation; the oracle's Multigrid.solve must reproduce them
   column by column.  A reversed sweep order, a wrong omega, a wrong transfer
   or a dropped coarse correction changes them.
+* Chebyshev semi-iteration (Sec. 3.4, Jacobi-Chebyshev on the mass
+  matrices): from x = 0 the error after k steps is
+      x* - x_k = T_k(sigma I - D^{-1} A / delta) / T_k(sigma) x*,
+  sigma = theta / delta, T_k the Chebyshev polynomial; the matrix polynomial
+  is built here by its three-term recurrence on dense matrices and must
+  reproduce the oracle's vector recurrence for every k.
 * Uzawa (Eq. Uzawa11): the two-line update is the block iteration
   x <- x + Pc^{-1} (b - G^(1,1) x) with Pc = [[tau Mhat, 0], [d_j M + tau L,
   -mu Shat]], G^(1,1) = [[tau M, (d_j M + tau L)^H], [d_j M + tau L,
@@ -168,3 +174,34 @@ def test_multigrid_pin_sees_plausible_mistakes():
     got = _mg_matrix(mg, n, 1)
     for wrong in (_vcycle_operator(lev, 0, 1.0, 2, 2, post_forward=True), _vcycle_operator(lev, 0, 0.9, 2, 2)):
         assert np.abs(got - wrong).max() > 1e-6 * np.abs(got).max()
+
+
+def _cheb_matrix(A, steps, bounds):
+    """x_k = (I - T_k(sigma I - E / delta) / T_k(sigma)) A^{-1}, E = D^{-1} A."""
+    lmin, lmax = bounds
+    theta, delta = 0.5 * (lmax + lmin), 0.5 * (lmax - lmin)
+    sigma = theta / delta
+    n = A.shape[0]
+    Z = sigma * np.eye(n) - np.diag(1.0 / np.diag(A)) @ A / delta
+    Tm, T = np.eye(n), Z.copy()          # T_0, T_1 of the matrix
+    tm, t = 1.0, sigma                   # T_0, T_1 at sigma
+    for _ in range(steps - 1):
+        Tm, T = T, 2.0 * Z @ T - Tm
+        tm, t = t, 2.0 * sigma * t - tm
+    return (np.eye(n) - T / t) @ np.linalg.inv(A)
+
+
+@pytest.mark.parametrize("space", ["q2", "q1"])
+def test_chebyshev_is_its_error_polynomial(space):
+    P = kkt.Problem("stokes", 2, 4, 0.2, 1e-2, 1e-2, 0.0, 1.0, None)
+    A = (P.Ms if space == "q2" else P.Mpr).toarray()
+    bounds = inexact.element_jacobi_bounds(2 if space == "q2" else 1)
+    b = np.random.default_rng(3).standard_normal(A.shape[0])
+    for steps in (1, 2, 5, 10):
+        ref = _cheb_matrix(A, steps, bounds) @ b
+        got = inexact.chebyshev(P.Ms if space == "q2" else P.Mpr, b, steps, bounds)
+        assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max(), steps
+    # a plausible mistake (bounds taken for the other element) changes the iterate
+    wrong = _cheb_matrix(A, 5, inexact.element_jacobi_bounds(1 if space == "q2" else 2)) @ b
+    assert np.abs(inexact.chebyshev(P.Ms if space == "q2" else P.Mpr, b, 5, bounds) - wrong).max() > 1e-6 * np.abs(wrong).max()
+
