@@ -165,6 +165,10 @@ __device__ __forceinline__ void q2_pw(int f, int& base, float w[3]) {
 
 template <class T, int SP, bool CONV, bool CW>
 __global__ void __launch_bounds__(1024, 1) mg_kernel(MGLaunch<T> L) {
+  // launched for the pressure operators only (no convection); the velocity
+  // multigrids, with or without convection, run in mg_q2b_kernel or the
+  // compile-time-sized kernel
+  static_assert(SP == 1 && !CONV && !CW, "mg_kernel serves the real pressure operators");
   __shared__ cpx<T> sw[100];
   __shared__ cpx<T> sdi[9];
   __shared__ T srs[9];
