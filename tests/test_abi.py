@@ -40,6 +40,44 @@ def test_struct_layouts_match_header_field_order():
     assert order == [f[0] for f in binding.Params._fields_]
 
 
+def _header_struct_fields(src, name):
+    """(field name, array length or 1) of `typedef struct { ... } name;` in
+    the header, comments removed."""
+    import re
+    end = src.index("} " + name + ";")
+    start = src.rindex("typedef struct {", 0, end)
+    body = re.sub(r"/\*.*?\*/", "", src[start + len("typedef struct {"):end], flags=re.S)
+    consts = {"PINT_PROF_CLASSES": binding.PROF_CLASSES and len(binding.PROF_CLASSES)}
+    out = []
+    for decl in body.split(";"):
+        decl = " ".join(decl.split())
+        if not decl:
+            continue
+        names = decl.split(None, 1)[1] if not decl.startswith(("long long", "unsigned")) else decl.split(None, 2)[2]
+        for n in names.split(","):
+            n = n.strip()
+            if "[" in n:
+                base, dim = n[:-1].split("[")
+                out.append((base.strip(), consts.get(dim.strip(), None) or int(dim)))
+            else:
+                out.append((n, 1))
+    return out
+
+
+@pytest.mark.parametrize("cname,pyname", [("pint_solve_info", "SolveInfo"), ("pint_sizes", "Sizes"),
+                                          ("pint_profile", "Profile"), ("pint_group_stats", "GroupStats"),
+                                          ("pint_server_params", "ServerParams"),
+                                          ("pint_server_stats", "ServerStats")])
+def test_other_structs_match_header(cname, pyname):
+    """Field order, array lengths and names of the result structures agree
+    between include/pint.h and the ctypes binding."""
+    fields = _header_struct_fields(open(binding.HEADER).read(), cname)
+    py = getattr(binding, pyname)._fields_
+    assert [f[0] for f in fields] == [f[0] for f in py]
+    for (name, n), (_, ctype) in zip(fields, py):
+        assert (getattr(ctype, "_length_", 1)) == n, name
+
+
 def test_default_params_and_argument_validation():
     if not os.path.exists(binding.LIB_PATH):
         pytest.skip("libpint.so not built")
